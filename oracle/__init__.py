@@ -1,0 +1,239 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product library never loads it, and it
+never loads the product library: the two share no code. What it computes and the
+passages it follows are documented in ``fe_oracle.c``; this module is argument
+marshalling (numpy <-> C) plus thin library-primitive steps (scipy's sparse direct
+solve) used by the pins.
+
+Functions whose parity with the paper is checked by the pin tests:
+  element_stiffness, assemble, spmv, sampled_product, block_jacobi, pcg,
+  fcg_mixed, adjoint_grad.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fe_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile fe_oracle.c with gcc (no FMA contraction, so results do not depend on
+    the host architecture's fused multiply-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_tet10_stiffness.argtypes = [_f64p, ctypes.c_double, ctypes.c_double, _f64p]
+        lib.oracle_pattern.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i64p, _i32p]
+        lib.oracle_pattern.restype = ctypes.c_int64
+        lib.oracle_assemble.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p,
+                                        _i64p, _i32p, _f64p]
+        lib.oracle_apply_bc.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _u8p]
+        lib.oracle_spmv.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, ctypes.c_int, _f64p, _f64p]
+        lib.oracle_spmv.restype = None
+        lib.oracle_sampled_product.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p,
+                                               _u8p, ctypes.c_int, _f64p, ctypes.c_int64, _i64p, _f64p]
+        lib.oracle_block_jacobi.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p]
+        lib.oracle_pcg.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int, _f64p, _f64p,
+                                   ctypes.c_double, ctypes.c_int, _i32p, _f64p]
+        lib.oracle_fcg_mixed.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int, _f64p,
+                                         _f64p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, _i32p, _i32p, _f64p]
+        lib.oracle_adjoint_grad.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p, _u8p,
+                                            ctypes.c_int, _f64p, _f64p, _f64p]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def element_stiffness(xe: np.ndarray, E: float, nu: float) -> np.ndarray:
+    """30x30 stiffness of one TET10 (nodes xe [10, 3], VTK order)."""
+    lib = _load()
+    xe = _c(xe, np.float64).reshape(30)
+    Ke = np.zeros(900)
+    rc = lib.oracle_tet10_stiffness(_p(xe, _f64p), float(E), float(nu), _p(Ke, _f64p))
+    if rc != 0:
+        raise ValueError("non-positive element Jacobian")
+    return Ke.reshape(30, 30)
+
+
+@dataclass
+class Assembled:
+    """Node-block CSR matrix: block b of row n couples nodes n and col[b]."""
+    n_nodes: int
+    rowptr: np.ndarray  # int64 [N+1]
+    col: np.ndarray     # int32 [nnzb]
+    vals: np.ndarray    # float64 [nnzb, 3, 3]
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.bsr_matrix((self.vals, self.col.astype(np.int64), self.rowptr),
+                             shape=(3 * self.n_nodes, 3 * self.n_nodes)).tocsr()
+
+    def dense(self) -> np.ndarray:
+        return self.to_scipy().toarray()
+
+
+def _mesh_arrays(mesh):
+    return (_c(mesh.coords, np.float64), _c(mesh.conn, np.int32), _c(mesh.young, np.float64),
+            _c(mesh.poisson, np.float64), _c(mesh.free, np.uint8))
+
+
+def assemble(mesh, apply_bc: bool = True, young=None) -> Assembled:
+    """K (or K_bc = P K P + (I - P) when apply_bc) of a mesh-like object with
+    attributes coords, conn, young, poisson, free."""
+    lib = _load()
+    coords, conn, E, nu, free = _mesh_arrays(mesh)
+    if young is not None:
+        E = _c(young, np.float64)
+    N, Ne = coords.shape[0], conn.shape[0]
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    nnzb = lib.oracle_pattern(N, Ne, _p(conn, _i32p), _p(rowptr, _i64p), None)
+    if nnzb < 0:
+        raise ValueError("bad connectivity")
+    col = np.zeros(nnzb, dtype=np.int32)
+    lib.oracle_pattern(N, Ne, _p(conn, _i32p), _p(rowptr, _i64p), _p(col, _i32p))
+    vals = np.zeros((nnzb, 3, 3))
+    rc = lib.oracle_assemble(N, _p(coords, _f64p), Ne, _p(conn, _i32p), _p(E, _f64p), _p(nu, _f64p),
+                             _p(rowptr, _i64p), _p(col, _i32p), _p(vals, _f64p))
+    if rc != 0:
+        raise ValueError("assembly failed (%d)" % rc)
+    if apply_bc:
+        lib.oracle_apply_bc(N, _p(rowptr, _i64p), _p(col, _i32p), _p(vals, _f64p), _p(free, _u8p))
+    return Assembled(N, rowptr, col, vals)
+
+
+def spmv(K: Assembled, x: np.ndarray) -> np.ndarray:
+    """y [N, R, 3] = K x for x [N, R, 3]."""
+    lib = _load()
+    x = _c(x, np.float64)
+    R = x.shape[1]
+    y = np.empty_like(x)
+    lib.oracle_spmv(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p), R,
+                    _p(x, _f64p), _p(y, _f64p))
+    return y
+
+
+def sampled_product(mesh, x: np.ndarray, nodes: np.ndarray) -> np.ndarray:
+    """Rows `nodes` of K_bc x, element by element, without full assembly: [S, R, 3]."""
+    lib = _load()
+    coords, conn, E, nu, free = _mesh_arrays(mesh)
+    x = _c(x, np.float64)
+    nodes = _c(nodes, np.int64)
+    R = x.shape[1]
+    ys = np.zeros((nodes.shape[0], R, 3))
+    rc = lib.oracle_sampled_product(coords.shape[0], _p(coords, _f64p), conn.shape[0], _p(conn, _i32p),
+                                    _p(E, _f64p), _p(nu, _f64p), _p(free, _u8p), R, _p(x, _f64p),
+                                    nodes.shape[0], _p(nodes, _i64p), _p(ys, _f64p))
+    if rc != 0:
+        raise ValueError("sampled product failed (%d)" % rc)
+    return ys
+
+
+def block_jacobi(K: Assembled) -> np.ndarray:
+    """Inverse 3x3 diagonal blocks [N, 3, 3]."""
+    lib = _load()
+    Minv = np.zeros((K.n_nodes, 3, 3))
+    rc = lib.oracle_block_jacobi(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p),
+                                 _p(Minv, _f64p))
+    if rc != 0:
+        raise ValueError("singular diagonal block (%d)" % rc)
+    return Minv
+
+
+def pcg(K: Assembled, f: np.ndarray, u0=None, tol: float = 1e-8, maxit: int = 100000, Minv=None):
+    """PCG with 3x3 block Jacobi for every case: returns (u, iters, true relres)."""
+    lib = _load()
+    f = _c(f, np.float64)
+    R = f.shape[1]
+    u = np.zeros_like(f) if u0 is None else _c(u0, np.float64).copy()
+    Minv = block_jacobi(K) if Minv is None else _c(Minv, np.float64)
+    iters = np.zeros(R, dtype=np.int32)
+    rel = np.zeros(R)
+    lib.oracle_pcg(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p), _p(Minv, _f64p), R,
+                   _p(f, _f64p), _p(u, _f64p), float(tol), int(maxit), _p(iters, _i32p), _p(rel, _f64p))
+    return u, iters, rel
+
+
+def fcg_mixed(K: Assembled, f: np.ndarray, u0=None, tol: float = 1e-8, max_outer: int = 10000,
+              n_inner: int = 30, eps_inner: float = 0.1, literal_beta: bool = False, Minv=None):
+    """Flexible CG (FP64) with FP32 inner block-Jacobi PCG: (u, outer, inner_total, relres)."""
+    lib = _load()
+    f = _c(f, np.float64)
+    R = f.shape[1]
+    u = np.zeros_like(f) if u0 is None else _c(u0, np.float64).copy()
+    Minv = block_jacobi(K) if Minv is None else _c(Minv, np.float64)
+    outer = np.zeros(R, dtype=np.int32)
+    inner = np.zeros(R, dtype=np.int32)
+    rel = np.zeros(R)
+    lib.oracle_fcg_mixed(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p), _p(Minv, _f64p),
+                         R, _p(f, _f64p), _p(u, _f64p), float(tol), int(max_outer), int(n_inner),
+                         float(eps_inner), int(bool(literal_beta)), _p(outer, _i32p), _p(inner, _i32p),
+                         _p(rel, _f64p))
+    return u, outer, inner, rel
+
+
+def adjoint_grad(mesh, u: np.ndarray, lam: np.ndarray, young=None) -> np.ndarray:
+    """g[e] = -sum_r (P lam_r)_e^T K_e (P u_r)_e  (derivative w.r.t. log E_e)."""
+    lib = _load()
+    coords, conn, E, nu, free = _mesh_arrays(mesh)
+    if young is not None:
+        E = _c(young, np.float64)
+    u = _c(u, np.float64)
+    lam = _c(lam, np.float64)
+    R = u.shape[1]
+    g = np.zeros(conn.shape[0])
+    rc = lib.oracle_adjoint_grad(coords.shape[0], _p(coords, _f64p), conn.shape[0], _p(conn, _i32p), _p(E, _f64p),
+                                 _p(nu, _f64p), _p(free, _u8p), R, _p(u, _f64p), _p(lam, _f64p), _p(g, _f64p))
+    if rc != 0:
+        raise ValueError("adjoint gradient failed (%d)" % rc)
+    return g
+
+
+def direct_solve(K: Assembled, f: np.ndarray) -> np.ndarray:
+    """Sparse direct solve of K u = f per case (scipy's SuperLU), u [N, R, 3]."""
+    import scipy.sparse.linalg as spla
+    A = K.to_scipy().tocsc()
+    lu = spla.splu(A)
+    N, R, _ = f.shape
+    # rows of A are ordered (node, component); move R to the last axis
+    rhs = np.ascontiguousarray(np.moveaxis(f, 1, 2)).reshape(3 * N, R)
+    sol = lu.solve(rhs)
+    return np.ascontiguousarray(np.moveaxis(sol.reshape(N, 3, R), 2, 1))
