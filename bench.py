@@ -1,0 +1,412 @@
+"""Benchmark: EBE product throughput (GDOF x cases / s) on the 70x70x35-hexahedra
+layered crust block (1,029,000 TET10 elements, 4,234,653 DOF), FP32, R = 16, plus
+the batched mixed-precision solve against the plain one-case FP64 PCG on the same
+mesh (case-solves / s at relative residual 1e-8).
+
+One timed step = one fe_ebe_apply of R = 16 load cases (the product of Eq. 3 that
+dominates the inner loop). Inputs stay resident in HBM; x and y (271 MB each) are
+larger than L2, so no L2 flush is needed between steps. Multi-GPU (torchrun):
+every rank holds the mesh and its own cases (case sharding, weak scaling, no
+data-path collective); rank 0 prints the line, value = all ranks' work / max time.
+
+--impl reference times the CPU oracle (assembled CSR product) on a bounded slab
+of the same workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EBE GDOF·cases/s and case-solves/s at 1e-8 residual; batched-mixed vs plain FP64"
+SHAPE = (70, 70, 35)
+R_MAIN = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the R / precision sweep")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(shape):
+    from paper_1710_08679_gb300 import meshgen as mg
+    m, iface = mg.crust_block(shape=shape, h=1000.0, jitter=0.15, seed=1)
+    return m, iface
+
+
+def ebe_flops_per_element(R: int) -> float:
+    """Algorithmic flops of the lean element product (multiply-add = 2):
+    774 per case and element plus 100 per element for geometry and Lame constants
+    (counted from the element arithmetic)."""
+    return 774.0 * R + 100.0
+
+
+def ebe_bytes(N: int, E: int, R: int, s: int) -> float:
+    """Algorithmic bytes per product: connectivity (40 B) and material (2s) per
+    element, coordinates (3s) per node, x read once and y written once."""
+    return E * (40.0 + 2 * s) + N * (3 * s + 2 * 3 * R * s)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock = 80.5
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded slab of the same mesh)
+# ---------------------------------------------------------------------------
+def oracle_slab(m, n_layers: int):
+    """Elements of the bottom `n_layers` hexahedron layers (hexahedra are stored
+    k-major, 6 tetrahedra each) with their nodes renumbered."""
+    nx, ny, _ = m.shape
+    ne = nx * ny * 6 * n_layers
+    conn = m.conn[:ne]
+    used = np.unique(conn)
+    remap = -np.ones(m.n_nodes, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    from paper_1710_08679_gb300 import meshgen as mg
+    return mg.Mesh(coords=m.coords[used], conn=remap[conn].astype(np.int32), young=m.young[:ne],
+                   poisson=m.poisson[:ne], free=m.free[used], shape=(nx, ny, n_layers), h=m.h, lengths=m.lengths)
+
+
+def cpu_baseline(m, R: int, reps: int = 3, n_layers: int = 4):
+    import oracle
+    sub = oracle_slab(m, n_layers)
+    t0 = time.perf_counter()
+    K = oracle.assemble(sub)
+    t_asm = time.perf_counter() - t0
+    from paper_1710_08679_gb300 import meshgen as mg
+    x = mg.random_vectors(sub.n_nodes, R, seed=100 + R)
+    oracle.spmv(K, x)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.spmv(K, x)
+    t = (time.perf_counter() - t0) / reps
+    return {"value": 3 * sub.n_nodes * R / t / 1e9, "unit": "GDOF·cases/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"assembled CSR product y = K_bc x of the bottom {n_layers} of 35 hexahedron layers "
+                       f"({sub.n_elem} elements, {3 * sub.n_nodes} DOF), R = {R}, FP64, mean of {reps}; "
+                       f"assembly {t_asm:.1f} s not included")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    m, _ = make_workload(SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x")))
+    import oracle
+    sub = oracle_slab(m, 4)
+    K = oracle.assemble(sub)
+    from paper_1710_08679_gb300 import meshgen as mg
+    x = mg.random_vectors(sub.n_nodes, R_MAIN, seed=100 + R_MAIN)
+    for _ in range(args.warmup):
+        oracle.spmv(K, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spmv(K, x)
+    t = time.perf_counter() - t0
+    val = 3 * sub.n_nodes * R_MAIN * args.steps / t / 1e9
+    out = {"metric": METRIC, "value": val, "unit": "GDOF·cases/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "crust_70x70x35_tet10_slab4", "R": R_MAIN, "mesh_elements": sub.n_elem,
+                      "mesh_dof": 3 * sub.n_nodes},
+           "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": val,
+                            "sample": f"assembled CSR product of the bottom 4 of 35 hexahedron layers "
+                                      f"({sub.n_elem} elements), R = {R_MAIN}, FP64"},
+           "e2e": {"value": val, "unit": "GDOF·cases/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def time_ebe(M, x, y, steps, warmup, torch):
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        M.ebe(x, out=y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.nvtx.range_push("timed")
+    ev[0].record(s)
+    for k in range(steps):
+        M.ebe(x, out=y)
+        ev[k + 1].record(s)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
+
+
+def slip_rhs(m, iface, R, M_ext, torch, fe):
+    """Split-node forces of R unit-slip patches, computed on the GPU with the EBE
+    product of each patch's hanging-wall elements: f = -P sum K_e s_e."""
+    from paper_1710_08679_gb300 import meshgen as mg
+    cases = mg.patch_grid_cases(m, iface)[:R]
+    f = torch.zeros((m.n_nodes, R, 3), dtype=torch.float64, device="cuda")
+    free = torch.from_numpy(m.free.astype(np.float64)).cuda()
+    for r, c in enumerate(cases):
+        sub = mg.Mesh(coords=m.coords, conn=m.conn[c.elems], young=m.young[c.elems], poisson=m.poisson[c.elems],
+                      free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
+        Ms = fe.Mesh.from_mesh(sub)
+        y = Ms.ebe(torch.from_numpy(np.ascontiguousarray(c.slip[:, None, :])).cuda())
+        f[:, r, :] = -y[:, 0, :] * free
+        Ms.close()
+    return f
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1710_08679_gb300 import fe
+    from paper_1710_08679_gb300 import meshgen as mg
+
+    shape = SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x"))
+    m, iface = make_workload(shape)
+    N, E = m.n_nodes, m.n_elem
+    M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
+    R = R_MAIN
+    v32, us32 = M.tune(R, "f32")
+    x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R + rank).astype(np.float32)).cuda()
+    y = torch.empty_like(x)
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[torch.cuda.current_device()]))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    total_ms, per = time_ebe(M, x, y, args.steps, args.warmup, torch)
+    clocks = sampler.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    units = 3.0 * N * R * args.steps * world
+    value = units / (total_ms * 1e-3) / 1e9
+    ms_step = total_ms / args.steps
+    ebe_ms = float(np.mean(per))
+
+    # e2e: host pinned x -> device, product, device -> host y, every step
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        M.ebe(xd, out=y)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e_steps = max(5, args.steps // 5)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(e_steps):
+        xd.copy_(xh, non_blocking=True)
+        M.ebe(xd, out=y)
+        yh.copy_(y, non_blocking=True)
+    t1.record()
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / e_steps
+    e2e = {"value": 3.0 * N * R * world / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF·cases/s",
+           "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)}
+
+    hbm, peak_src = load_peaks()
+    flops = E * ebe_flops_per_element(R)
+    achieved_tf = flops / (ebe_ms * 1e-3) / 1e12
+    bytes_alg = ebe_bytes(N, E, R, 4)
+    achieved_gbs = bytes_alg / (ebe_ms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "ebe_traffic.json")
+    if os.path.exists(tp):
+        try:
+            tj = json.load(open(tp))
+            if tj.get("variant") == int(v32) and tj.get("shape") == list(shape) and tj.get("R") == R:
+                traffic = tj.get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "fe_ebe_apply (y init + %s EBE kernel)" % ("tiled" if v32 else "direct"),
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                        "peak_source": peak_src, "algorithmic_bytes": bytes_alg}}
+
+    out = {"metric": METRIC, "value": value, "unit": "GDOF·cases/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "crust_%dx%dx%d_tet10_R%d_fp32_ebe" % (shape + (R,)), "mesh_elements": E,
+                      "mesh_dof": 3 * N, "R": R, "kernel_variant": int(v32),
+                      "l2": "inputs larger than L2 (x and y %d MB each), no flush" % (x.numel() * 4 // 2 ** 20),
+                      "parallelism": "case-sharded replicas x%d" % world},
+           "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "clocks": clocks}
+
+    if not args.no_sweep:
+        sweep = {}
+        for dt in ("f32", "f64"):
+            for RR in (1, 4, 8, 16, 32):
+                M.tune(RR, dt)
+                tt = torch.float32 if dt == "f32" else torch.float64
+                xx = torch.from_numpy(mg.random_vectors(N, RR, seed=100 + RR)).to("cuda", tt)
+                yy = torch.empty_like(xx)
+                ms, _ = time_ebe(M, xx, yy, 5 if dt == "f64" else 10, 2, torch)
+                n = 5 if dt == "f64" else 10
+                sweep[f"{dt}_R{RR}"] = {"GDOF_cases_per_s": 3.0 * N * RR / (ms / n * 1e-3) / 1e9,
+                                        "ms": ms / n, "variant": M.get_variant(RR, dt)[1]}
+                del xx, yy
+        out["ebe_sweep"] = sweep
+
+    if not args.no_solve:
+        out["solve"] = run_solves(m, iface, M, torch, fe, world)
+
+    if rank == 0 and not args.no_cpu and world == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline(m, R)
+        except Exception as exc:  # report, never fail the line
+            out["cpu_baseline"] = {"error": str(exc)[:200]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_solves(m, iface, M, torch, fe, world):
+    """Batched mixed FCG (R = 16 unit-slip patches) vs plain FP64 PCG, one case
+    at a time, on the same mesh; both to true relative residual 1e-8."""
+    R = 16
+    f = slip_rhs(m, iface, R, M, torch, fe)
+    M.tune(R, "f64")
+    M.tune(1, "f64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, stats, st = M.solve(f, solver="fcg_mixed", tol=1e-8, raise_on_fail=False)
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    ok = all(s["relres"] <= 1e-8 for s in stats)
+    # plain FP64 PCG, one case at a time (two cases timed, per-case time averaged)
+    n_plain = 2
+    t_plain = []
+    plain_stats = []
+    for r in range(n_plain):
+        fr = f[:, r:r + 1, :].contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ur, sr, _ = M.solve(fr, solver="pcg64", tol=1e-8, raise_on_fail=False)
+        torch.cuda.synchronize()
+        t_plain.append(time.perf_counter() - t0)
+        plain_stats.append(sr[0])
+        du = torch.linalg.norm(ur[:, 0] - u[:, r]) / torch.linalg.norm(ur[:, 0])
+        plain_stats[-1]["rel_diff_vs_mixed"] = float(du)
+    mixed_rate = R / t_mixed
+    plain_rate = 1.0 / float(np.mean(t_plain))
+    return {"workload": "crust_70x70x35_tet10 16 unit-slip patches (4x4 grid, 2x2 km)",
+            "mixed_fcg": {"case_solves_per_s": mixed_rate * world, "seconds": t_mixed, "all_converged": ok,
+                          "outer": [s["outer"] for s in stats], "inner": [s["inner"] for s in stats],
+                          "relres_max": max(s["relres"] for s in stats), "status": int(st)},
+            "plain_pcg64_one_case": {"case_solves_per_s": plain_rate * world, "seconds_per_case": float(np.mean(t_plain)),
+                                     "iters": [s["outer"] for s in plain_stats],
+                                     "relres": [s["relres"] for s in plain_stats],
+                                     "rel_diff_vs_mixed": [s["rel_diff_vs_mixed"] for s in plain_stats]},
+            "speedup": mixed_rate / plain_rate}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

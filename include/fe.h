@@ -1,0 +1,220 @@
+/*
+ * fe.h -- C ABI of libfe: matrix-free element-by-element (EBE) elasticity operator
+ * on 10-node tetrahedra for R load cases at once, and the conjugate-gradient
+ * solvers built on it, for NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of Yamaguchi, Fujita, Ichimura, Hori, Lalith and Nakajima,
+ * "Implicit Low-Order Unstructured Finite-Element Multiple Simulation Enhanced by
+ * Dense Computation using OpenACC": static linear elasticity (Sec. 2, Eq. 1a-1c)
+ * discretised with second-order tetrahedra into K u = f (Eq. 2); the product
+ * f = sum_i Q_i K_i Q_i^T u with element matrices recomputed on every call from
+ * node coordinates and material (Eq. 3); R right-hand sides solved together with
+ * the case index innermost (Sec. 3.1); a flexible CG whose preconditioner is an
+ * inner block-Jacobi CG run in single precision (Algorithm 1, Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns fe_status; none throws, aborts or traps. On failure
+ *     fe_last_error() returns a message (thread-local, valid until the next call
+ *     on the same thread).
+ *   - Pointers named *_dev are device pointers on the mesh's device, owned by the
+ *     caller, contiguous, aligned to at least 16 bytes. Host pointers are read
+ *     during the call only.
+ *   - Multi-vectors are laid out [node][case][component] ("[N][R][3]"): the 3R
+ *     values of one node are contiguous, so neighbouring threads that work on
+ *     different cases of one node touch neighbouring addresses.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - Element geometry is straight-sided: the element map is affine, defined by
+ *     the 4 corner nodes; edge nodes must lie at the midpoints of their edges.
+ *   - Node order inside an element is VTK's: corners 0..3, then the midpoints of
+ *     edges (0,1), (1,2), (2,0), (0,3), (1,3), (2,3).
+ *   - Dirichlet conditions are homogeneous: constrained DOFs hold u = 0, and the
+ *     operator applied is K_bc = P K P + (I - P), P = diag(free mask).
+ */
+#ifndef FE_H_
+#define FE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FE_OK = 0,
+  FE_EINVAL = 1,      /* invalid argument or mesh; nothing was launched */
+  FE_ENOMEM = 2,      /* device or host allocation failed */
+  FE_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
+  FE_ENOCONV = 4,     /* a solve hit its iteration cap before the tolerance */
+  FE_EBREAKDOWN = 5,  /* a solve met a non-positive curvature or a NaN/Inf */
+  FE_ETIMEOUT = 6     /* a bounded device-side wait gave up */
+} fe_status;
+
+typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
+
+typedef enum {
+  FE_SOLVER_PCG64 = 0,      /* FP64 CG with 3x3 block Jacobi (the plain baseline) */
+  FE_SOLVER_FCG_MIXED = 1   /* FP64 flexible CG, FP32 inner block-Jacobi CG (Algorithm 1) */
+} fe_solver;
+
+typedef struct fe_mesh fe_mesh;   /* opaque, library-owned */
+
+/* Solver options (Algorithm 1; inner-loop defaults from the paper's table of
+ * loop settings, level 0: tolerance 0.1, 30 iterations). */
+typedef struct {
+  int32_t solver;        /* fe_solver */
+  double tol;            /* stop case r when ||f_r - K u_r|| / ||f_r|| <= tol (1e-8) */
+  int32_t max_outer;     /* cap on outer iterations (PCG64: CG iterations) */
+  int32_t n_inner;       /* cap on inner steps per outer iteration (30) */
+  double eps_inner;      /* inner stop: max over active cases ||e||^2/||rbar||^2 <= eps_inner (0.1) */
+  int32_t use_graph;     /* 1: replay one outer iteration from a captured CUDA graph */
+  int32_t literal_beta;  /* 1: the printed beta = (z,q)/rho; 0: flexible CG beta (default) */
+  int32_t check_every;   /* outer iterations between host reads of the convergence flags (>= 1) */
+  int32_t verbose;       /* reserved, 0 */
+} fe_solve_opts;
+
+/* Per-case results of fe_pcg_solve. */
+typedef struct {
+  int32_t outer_iters;   /* outer iterations (PCG64: CG iterations) this case took */
+  int32_t inner_iters;   /* inner steps summed over outer iterations (0 for PCG64) */
+  double relres;         /* true relative residual ||f - K u|| / ||f|| at exit (FP64 product) */
+  int32_t status;        /* FE_OK, FE_ENOCONV or FE_EBREAKDOWN for this case */
+  int32_t pad;
+} fe_solve_stats;
+
+/* Message of the last failure on this thread ("" if none). */
+const char* fe_last_error(void);
+
+/* Library version string. */
+const char* fe_version(void);
+
+/* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
+ * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1. */
+void fe_solve_opts_default(fe_solve_opts* opts);
+
+/*
+ * fe_mesh_create -- validate a TET10 mesh and make its device copy.
+ *   n_nodes, coords   host double [N][3], metres
+ *   n_elem, conn      host int32 [E][10], 0-based node ids, VTK order
+ *   young, poisson    host double [E]: Young's modulus (Pa, > 0) and Poisson ratio
+ *                     (-1 < nu < 0.5) per element (isotropic C_ijkl of Eq. 1b)
+ *   free_mask         host uint8 [N][3]: 1 = free DOF, 0 = fixed at zero
+ *   device            CUDA device ordinal the mesh lives on
+ *   stream            stream for the uploads (the call returns after they finish)
+ * Checks: sizes, finite values, node ids in range and distinct within an
+ * element, positive volumes, edge nodes at midpoints (relative 1e-6 of the
+ * element's size), material ranges. Returns FE_EINVAL with a message naming the
+ * first offending element or node. *out receives the handle (NULL on failure).
+ */
+fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,
+                         const double* young, const double* poisson, const uint8_t* free_mask,
+                         int32_t device, void* stream, fe_mesh** out);
+
+/* Releases every device resource of the mesh (synchronises the device). NULL is a no-op. */
+void fe_mesh_destroy(fe_mesh* mesh);
+
+/* Node and element counts of a mesh. */
+fe_status fe_mesh_info(const fe_mesh* mesh, int64_t* n_nodes, int64_t* n_elem);
+
+/*
+ * fe_mesh_set_log_young -- replace the per-element Young's moduli by exp(logE).
+ * logE_dev: device double [E]. The block-Jacobi preconditioner is rebuilt on
+ * the next solve. Used by gradient checks and by the adjoint workflow
+ * (m_e = log E_e, Poisson ratio unchanged).
+ */
+fe_status fe_mesh_set_log_young(fe_mesh* mesh, const double* logE_dev, void* stream);
+
+/*
+ * fe_ebe_apply -- y = K_bc x for R cases (Eq. 3 with the multiple-vector layout
+ * of Sec. 3.1).
+ *   R        number of cases, 1 <= R <= 64
+ *   dtype    FE_F64: double vectors, FP64 arithmetic;
+ *            FE_F32: float vectors, FP32 arithmetic and FP32 accumulation
+ *   x_dev    device [N][R][3] of dtype, read only
+ *   y_dev    device [N][R][3] of dtype, overwritten; must not alias x_dev
+ * Element matrices are never stored: each call recomputes the element geometry
+ * and Lame constants from the node coordinates and (E, nu). Summation order of
+ * the element contributions is not fixed (atomic accumulation), so results are
+ * reproducible to rounding only.
+ */
+fe_status fe_ebe_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x_dev, void* y_dev,
+                       void* stream);
+
+/* EBE kernel variants (both compute fe_ebe_apply's result):
+ *   FE_EBE_DIRECT  one thread per (element, case), inputs gathered from global
+ *                  memory, results added with global atomics (the paper's GPU
+ *                  port keeps atomics rather than element colouring, Sec. 3.2.2);
+ *   FE_EBE_TILED   consecutive elements (in the library's locality order) form a
+ *                  tile; the tile's node values are staged in shared memory, the
+ *                  element products accumulate there, and each tile node gets one
+ *                  global atomic add per value. */
+typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1 } fe_ebe_variant;
+
+/*
+ * fe_ebe_set_variant -- choose the kernel fe_ebe_apply (and the solvers) use for
+ * (R, dtype) on this mesh. tile_elems (1..4096) applies to FE_EBE_TILED; the
+ * tiling is built on first use (host work, synchronous on `stream`). Fails with
+ * FE_EINVAL if the tile's shared-memory footprint exceeds the device limit.
+ */
+fe_status fe_ebe_set_variant(fe_mesh* mesh, int32_t R, fe_dtype dtype, int32_t variant, int32_t tile_elems,
+                             void* stream);
+
+/* Current kernel for (R, dtype): *variant (fe_ebe_variant) and *tile_elems (0 for direct). */
+fe_status fe_ebe_get_variant(const fe_mesh* mesh, int32_t R, fe_dtype dtype, int32_t* variant,
+                             int32_t* tile_elems);
+
+/*
+ * fe_ebe_tune -- autotuner: times the direct kernel and the tiled kernel at
+ * 24/48/96/192/384 elements per tile (where it fits) for (R, dtype) on this mesh,
+ * using library-owned scratch vectors, and selects the fastest. Synchronous.
+ * *variant receives 0 for direct or the chosen tile size; *us its time per
+ * product in microseconds.
+ */
+fe_status fe_ebe_tune(fe_mesh* mesh, int32_t R, fe_dtype dtype, void* stream, int32_t* variant, int32_t* us);
+
+/*
+ * fe_pcg_solve -- solve K_bc u_r = f_r for R cases at once (Algorithm 1 with the
+ * inner loop at level 0 only, or plain block-Jacobi PCG).
+ *   f_dev    device double [N][R][3]; constrained entries are ignored (treated as 0)
+ *   u_dev    device double [N][R][3]; in: initial guess, out: solution
+ *   opts     host; NULL = defaults
+ *   stats    host [R], written on return
+ * Synchronous: returns when u and stats are final. Each case stops on its own
+ * (per-case masking): once ||f_r - K u_r||/||f_r|| <= tol, checked with an FP64
+ * product, its vectors are frozen. Cases with f_r = 0 return u_r = 0 at once.
+ * Returns FE_OK when every case converged, FE_ENOCONV if any hit max_outer, or
+ * FE_EBREAKDOWN if any broke down; u then holds the last iterate of each case.
+ * Library-owned workspace (about 12 vectors of [N][R][3], FP64 and FP32) is
+ * allocated on first use per R and kept with the mesh.
+ */
+fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* f_dev, double* u_dev,
+                       const fe_solve_opts* opts, fe_solve_stats* stats, void* stream);
+
+/*
+ * fe_block_jacobi -- the 3x3 block-Jacobi preconditioner M^-1 = diag3x3[K_bc]^-1
+ * of Algorithm 1 (lines 1-3) and of the PCG baseline, built on first use from
+ * the element matrices' diagonal blocks (closed form, FP64) with constrained
+ * rows and columns set to the identity.
+ *   binv_dev  device double [N][3][3], overwritten with the inverse blocks
+ * Fails with FE_EINVAL if a free node has a singular or indefinite block.
+ */
+fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void* stream);
+
+/*
+ * fe_adjoint_grad -- element sensitivities for m_e = log E_e:
+ *   g_e = - sum_r (P lambda_r)_e^T K_e (P u_r)_e
+ * which is dJ/dm_e when K_bc lambda_r = dJ/du_r (adjoint state) and
+ * K_bc u_r = f_r. No counterpart in the paper (it is an addition of this
+ * library); the element product is the same EBE kernel, reduced per element
+ * instead of scattered.
+ *   u_dev, lambda_dev  device double [N][R][3]
+ *   g_elem_dev         device double [E], overwritten
+ */
+fe_status fe_adjoint_grad(const fe_mesh* mesh, int32_t R, const double* u_dev, const double* lambda_dev,
+                          double* g_elem_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_H_ */

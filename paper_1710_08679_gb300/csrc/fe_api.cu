@@ -1,0 +1,413 @@
+// C ABI of libfe: mesh creation and validation, EBE product entry point, errors.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fe_internal.cuh"
+
+namespace fe {
+
+static thread_local std::string g_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+}
+
+void clear_error() { g_error.clear(); }
+
+DeviceGuard::DeviceGuard(int dev) {
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != dev) FE_CUDA(cudaSetDevice(dev));
+}
+
+DeviceGuard::~DeviceGuard() {
+  int cur = -1;
+  if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+void DevBuf::alloc(size_t n) {
+  release();
+  if (n == 0) return;
+  cudaError_t e = cudaMalloc(&ptr, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    set_error("cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    throw Failure{FE_ENOMEM};
+  }
+  bytes = n;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// Runs f, converting library failures and C++ exceptions into a status.
+template <typename F>
+static fe_status guarded(F&& f) {
+  try {
+    clear_error();
+    f();
+    return FE_OK;
+  } catch (const Failure& x) {
+    return x.status;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FE_ENOMEM;
+  } catch (...) {
+    set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// element order and tiles
+// ---------------------------------------------------------------------------
+
+static uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+
+// Morton (Z-curve) order of element centroids: neighbouring elements get
+// neighbouring indices, so element tiles are compact and node data is reused
+// from L2 while it is hot.
+static std::vector<int64_t> morton_order(int64_t N, const double* xyz, int64_t E, const int32_t* conn) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t n = 0; n < N; ++n)
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = std::min(lo[i], xyz[3 * n + i]);
+      hi[i] = std::max(hi[i], xyz[3 * n + i]);
+    }
+  double scale = 0.0;
+  for (int i = 0; i < 3; ++i) scale = std::max(scale, hi[i] - lo[i]);
+  scale = scale > 0 ? (double)((1 << 21) - 1) / scale : 0.0;
+  std::vector<uint64_t> key((size_t)E);
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t k = 0;
+    for (int i = 0; i < 3; ++i) {
+      double c = 0.0;
+      for (int a = 0; a < 4; ++a) c += xyz[3 * (int64_t)conn[10 * e + a] + i];
+      c = 0.25 * c;
+      uint64_t q = (uint64_t)std::llround((c - lo[i]) * scale);
+      k |= spread3(q) << i;
+    }
+    key[(size_t)e] = k;
+  }
+  std::vector<int64_t> order((size_t)E);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key[(size_t)a] < key[(size_t)b]; });
+  return order;
+}
+
+const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
+  FE_REQUIRE(tile_elems >= 1 && tile_elems <= 4096, "tile size %d out of range", tile_elems);
+  auto found = m->tilings.find(tile_elems);
+  if (found != m->tilings.end()) return found->second.get();
+  std::unique_ptr<Tiling> tp(new Tiling());
+  Tiling& t = *tp;
+  const int64_t E = m->n_elem;
+  const int64_t nt = (E + tile_elems - 1) / tile_elems;
+  std::vector<int32_t> ptr((size_t)nt + 1, 0);
+  std::vector<int32_t> ids;
+  std::vector<uint16_t> lconn((size_t)E * 10);
+  ids.reserve((size_t)E * 3);
+  std::vector<int32_t> buf;
+  std::vector<uint8_t> own;
+  own.reserve((size_t)E * 3);
+  std::vector<uint8_t> seen((size_t)m->n_nodes, 0);
+  int max_nodes = 0;
+  for (int64_t ti = 0; ti < nt; ++ti) {
+    const int64_t e0 = ti * tile_elems, e1 = std::min(E, e0 + tile_elems);
+    buf.assign(m->conn_host.begin() + 10 * e0, m->conn_host.begin() + 10 * e1);
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    FE_REQUIRE(buf.size() <= 65535, "tile too large");
+    max_nodes = std::max(max_nodes, (int)buf.size());
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = 0; a < 10; ++a) {
+        const int32_t g = m->conn_host[(size_t)(10 * e + a)];
+        lconn[(size_t)(10 * e + a)] = (uint16_t)(std::lower_bound(buf.begin(), buf.end(), g) - buf.begin());
+      }
+    FE_REQUIRE(ids.size() + buf.size() < (size_t)INT32_MAX, "tiling too large");
+    ids.insert(ids.end(), buf.begin(), buf.end());
+    for (int32_t g : buf) {
+      own.push_back(seen[(size_t)g] ? 0 : 1);
+      seen[(size_t)g] = 1;
+    }
+    ptr[(size_t)ti + 1] = (int32_t)ids.size();
+  }
+  t.node_ptr.alloc(ptr.size() * sizeof(int32_t));
+  t.node_ids.alloc(ids.size() * sizeof(int32_t));
+  t.lconn.alloc(lconn.size() * sizeof(uint16_t));
+  t.node_own.alloc(own.size());
+  FE_CUDA(cudaMemcpyAsync(t.node_own.ptr, own.data(), own.size(), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(t.node_ptr.ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(t.node_ids.ptr, ids.data(), ids.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(t.lconn.ptr, lconn.data(), lconn.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  t.tile_elems = tile_elems;
+  t.max_nodes = max_nodes;
+  t.n_tiles = nt;
+  const Tiling* out = tp.get();
+  m->tilings[tile_elems] = std::move(tp);
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// materials upload (internal element order)
+// ---------------------------------------------------------------------------
+static void upload_materials(fe_mesh* m, cudaStream_t s) {
+  const int64_t E = m->n_elem;
+  std::vector<double> m64((size_t)E * 2);
+  std::vector<float> m32((size_t)E * 2);
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t src = m->perm_host[(size_t)e];
+    m64[2 * e] = m->young_host[(size_t)src];
+    m64[2 * e + 1] = m->poisson_host[(size_t)src];
+    m32[2 * e] = (float)m64[2 * e];
+    m32[2 * e + 1] = (float)m64[2 * e + 1];
+  }
+  FE_CUDA(cudaMemcpyAsync(m->mat64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(m->mat32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  m->jacobi_ready = false;
+}
+
+}  // namespace fe
+
+template <>
+fe::MeshView<double> fe_mesh::view<double>() const {
+  return {n_nodes, n_elem, conn.as<int32_t>(), xyz64.as<double>(), mat64.as<double>(), nmask.as<uint8_t>()};
+}
+template <>
+fe::MeshView<float> fe_mesh::view<float>() const {
+  return {n_nodes, n_elem, conn.as<int32_t>(), xyz32.as<float>(), mat32.as<float>(), nmask.as<uint8_t>()};
+}
+
+using namespace fe;
+
+extern "C" {
+
+const char* fe_last_error(void) { return g_error.c_str(); }
+
+const char* fe_version(void) { return "libfe 0.1 (sm_103a)"; }
+
+void fe_solve_opts_default(fe_solve_opts* o) {
+  if (!o) return;
+  o->solver = FE_SOLVER_FCG_MIXED;
+  o->tol = 1e-8;
+  o->max_outer = 20000;
+  o->n_inner = 30;
+  o->eps_inner = 0.1;
+  o->use_graph = 1;
+  o->literal_beta = 0;
+  o->check_every = 1;
+  o->verbose = 0;
+}
+
+fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,
+                         const double* young, const double* poisson, const uint8_t* free_mask, int32_t device,
+                         void* stream, fe_mesh** out) {
+  if (out) *out = nullptr;
+  fe_mesh* m = nullptr;
+  fe_status st = guarded([&] {
+    FE_REQUIRE(out != nullptr, "out is NULL");
+    FE_REQUIRE(coords && conn && young && poisson && free_mask, "NULL input array");
+    FE_REQUIRE(n_nodes > 0 && n_nodes < (int64_t)INT32_MAX, "n_nodes = %lld out of range", (long long)n_nodes);
+    FE_REQUIRE(n_elem > 0 && n_elem < ((int64_t)1 << 40), "n_elem = %lld out of range", (long long)n_elem);
+    for (int64_t i = 0; i < 3 * n_nodes; ++i)
+      FE_REQUIRE(std::isfinite(coords[i]), "coordinate of node %lld is not finite", (long long)(i / 3));
+    for (int64_t i = 0; i < 3 * n_nodes; ++i)
+      FE_REQUIRE(free_mask[i] <= 1, "free_mask of node %lld is not 0/1", (long long)(i / 3));
+    for (int64_t e = 0; e < n_elem; ++e) {
+      const int32_t* ce = conn + 10 * e;
+      for (int a = 0; a < 10; ++a) {
+        FE_REQUIRE(ce[a] >= 0 && ce[a] < n_nodes, "element %lld: node id %d out of range", (long long)e, ce[a]);
+        for (int b = 0; b < a; ++b)
+          FE_REQUIRE(ce[a] != ce[b], "element %lld: node %d repeated", (long long)e, ce[a]);
+      }
+      FE_REQUIRE(std::isfinite(young[e]) && young[e] > 0.0, "element %lld: Young's modulus must be > 0",
+                 (long long)e);
+      FE_REQUIRE(std::isfinite(poisson[e]) && poisson[e] > -1.0 && poisson[e] < 0.5,
+                 "element %lld: Poisson ratio must lie in (-1, 0.5)", (long long)e);
+      const double* x0 = coords + 3 * (int64_t)ce[0];
+      double d[3][3];
+      double hmax = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) {
+          d[k][i] = coords[3 * (int64_t)ce[k + 1] + i] - x0[i];
+          hmax = std::max(hmax, std::fabs(d[k][i]));
+        }
+      const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                         d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                         d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+      FE_REQUIRE(det > 1e-12 * hmax * hmax * hmax, "element %lld: non-positive volume (inverted or flat)",
+                 (long long)e);
+      static const int EA[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+      for (int q = 0; q < 6; ++q)
+        for (int i = 0; i < 3; ++i) {
+          const double mid = 0.5 * (coords[3 * (int64_t)ce[EA[q][0]] + i] + coords[3 * (int64_t)ce[EA[q][1]] + i]);
+          FE_REQUIRE(std::fabs(coords[3 * (int64_t)ce[4 + q] + i] - mid) <= 1e-6 * hmax,
+                     "element %lld: edge node %d is not at its edge midpoint (elements must be straight-sided)",
+                     (long long)e, 4 + q);
+        }
+    }
+    int ndev = 0;
+    FE_CUDA(cudaGetDeviceCount(&ndev));
+    FE_REQUIRE(device >= 0 && device < ndev, "device %d not present (%d devices)", device, ndev);
+    DeviceGuard dg(device);
+    cudaStream_t s = (cudaStream_t)stream;
+    m = new fe_mesh();
+    m->device = device;
+    m->n_nodes = n_nodes;
+    m->n_elem = n_elem;
+    std::memset(m->variant, -1, sizeof(m->variant));
+    m->perm_host = morton_order(n_nodes, coords, n_elem, conn);
+    m->conn_host.resize((size_t)n_elem * 10);
+    for (int64_t e = 0; e < n_elem; ++e)
+      std::memcpy(&m->conn_host[(size_t)e * 10], conn + 10 * m->perm_host[(size_t)e], 10 * sizeof(int32_t));
+    m->young_host.assign(young, young + n_elem);
+    m->poisson_host.assign(poisson, poisson + n_elem);
+    std::vector<float> xyz32((size_t)n_nodes * 3);
+    for (int64_t i = 0; i < 3 * n_nodes; ++i) xyz32[(size_t)i] = (float)coords[i];
+    std::vector<uint8_t> nm((size_t)n_nodes);
+    for (int64_t n = 0; n < n_nodes; ++n)
+      nm[(size_t)n] = (uint8_t)(free_mask[3 * n] | (free_mask[3 * n + 1] << 1) | (free_mask[3 * n + 2] << 2));
+    m->conn.alloc((size_t)n_elem * 10 * sizeof(int32_t));
+    m->xyz64.alloc((size_t)n_nodes * 3 * sizeof(double));
+    m->xyz32.alloc((size_t)n_nodes * 3 * sizeof(float));
+    m->mat64.alloc((size_t)n_elem * 2 * sizeof(double));
+    m->mat32.alloc((size_t)n_elem * 2 * sizeof(float));
+    m->nmask.alloc((size_t)n_nodes);
+    m->perm.alloc((size_t)n_elem * sizeof(int64_t));
+    m->own_elem.alloc((size_t)n_elem * sizeof(uint16_t));
+    {
+      std::vector<uint16_t> ow((size_t)n_elem, 0);
+      std::vector<uint8_t> seen((size_t)n_nodes, 0);
+      for (int64_t e = 0; e < n_elem; ++e)
+        for (int a = 0; a < 10; ++a) {
+          const int32_t g = m->conn_host[(size_t)(10 * e + a)];
+          if (!seen[(size_t)g]) {
+            seen[(size_t)g] = 1;
+            ow[(size_t)e] |= (uint16_t)(1u << a);
+          }
+        }
+      FE_CUDA(cudaMemcpyAsync(m->own_elem.ptr, ow.data(), ow.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+      FE_CUDA(cudaStreamSynchronize(s));
+    }
+    FE_CUDA(cudaMemcpyAsync(m->conn.ptr, m->conn_host.data(), m->conn.bytes, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaMemcpyAsync(m->xyz64.ptr, coords, m->xyz64.bytes, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaMemcpyAsync(m->xyz32.ptr, xyz32.data(), m->xyz32.bytes, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaMemcpyAsync(m->nmask.ptr, nm.data(), m->nmask.bytes, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaMemcpyAsync(m->perm.ptr, m->perm_host.data(), m->perm.bytes, cudaMemcpyHostToDevice, s));
+    upload_materials(m, s);
+    *out = m;
+  });
+  if (st != FE_OK) {
+    delete m;
+    if (out) *out = nullptr;
+  }
+  return st;
+}
+
+void fe_mesh_destroy(fe_mesh* m) {
+  if (!m) return;
+  try {
+    DeviceGuard dg(m->device);
+    cudaDeviceSynchronize();
+    free_solver_work(m);
+    delete m;
+  } catch (...) {
+  }
+}
+
+fe_status fe_mesh_info(const fe_mesh* m, int64_t* n_nodes, int64_t* n_elem) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    if (n_nodes) *n_nodes = m->n_nodes;
+    if (n_elem) *n_elem = m->n_elem;
+  });
+}
+
+fe_status fe_ebe_apply(const fe_mesh* m, int32_t R, fe_dtype dtype, const void* x, void* y, void* stream) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range [1, 64]", R);
+    FE_REQUIRE(dtype == FE_F64 || dtype == FE_F32, "unknown dtype %d", (int)dtype);
+    FE_REQUIRE(x != nullptr && y != nullptr, "NULL vector");
+    FE_REQUIRE(x != y, "x and y must not alias");
+    FE_REQUIRE(((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0, "vectors must be 16-byte aligned");
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == FE_F64)
+      ebe_apply<double>(m, R, static_cast<const double*>(x), static_cast<double*>(y), s);
+    else
+      ebe_apply<float>(m, R, static_cast<const float*>(x), static_cast<float*>(y), s);
+  });
+}
+
+fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t variant, int32_t tile_elems,
+                             void* stream) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
+    FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED, "unknown variant %d", variant);
+    DeviceGuard dg(m->device);
+    if (variant == FE_EBE_TILED) {
+      get_tiling(m, tile_elems, (cudaStream_t)stream);
+      FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32),
+                 "tile of %d elements does not fit in shared memory for R = %d", tile_elems, R);
+      ebe_set_variant(m, R, dtype == FE_F32, tile_elems);
+    } else {
+      ebe_set_variant(m, R, dtype == FE_F32, 0);
+    }
+  });
+}
+
+fe_status fe_ebe_get_variant(const fe_mesh* m, int32_t R, fe_dtype dtype, int32_t* variant, int32_t* tile_elems) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
+    const int v = ebe_get_variant(m, R, dtype == FE_F32);
+    if (variant) *variant = v > 0 ? FE_EBE_TILED : FE_EBE_DIRECT;
+    if (tile_elems) *tile_elems = v > 0 ? v : 0;
+  });
+}
+
+fe_status fe_mesh_set_log_young(fe_mesh* m, const double* logE_dev, void* stream) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr && logE_dev != nullptr, "NULL argument");
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> le((size_t)m->n_elem);
+    FE_CUDA(cudaMemcpyAsync(le.data(), logE_dev, le.size() * 8, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    for (int64_t e = 0; e < m->n_elem; ++e) {
+      const double v = std::exp(le[(size_t)e]);
+      FE_REQUIRE(std::isfinite(v) && v > 0.0, "exp(logE) of element %lld is not a positive finite number",
+                 (long long)e);
+      m->young_host[(size_t)e] = v;
+    }
+    upload_materials(m, s);
+  });
+}
+
+}  // extern "C"

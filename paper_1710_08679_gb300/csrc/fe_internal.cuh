@@ -1,0 +1,152 @@
+// Internal declarations of libfe (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fe.h"
+
+namespace fe {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Failure {
+  fe_status status;
+};
+
+#define FE_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t err__ = (call);                                                           \
+    if (err__ != cudaSuccess) {                                                           \
+      ::fe::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err__), __FILE__, \
+                      __LINE__);                                                          \
+      throw ::fe::Failure{FE_ECUDA};                                                      \
+    }                                                                                     \
+  } while (0)
+
+#define FE_CHECK_LAUNCH() FE_CUDA(cudaGetLastError())
+
+#define FE_REQUIRE(cond, ...)          \
+  do {                                 \
+    if (!(cond)) {                     \
+      ::fe::set_error(__VA_ARGS__);    \
+      throw ::fe::Failure{FE_EINVAL};  \
+    }                                  \
+  } while (0)
+
+// Sets the mesh's device current for the scope and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+};
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  void alloc(size_t n);
+  void release();
+  template <typename T>
+  T* as() const { return static_cast<T*>(ptr); }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Pointers a kernel needs to evaluate element products in precision T.
+template <typename T>
+struct MeshView {
+  int64_t n_nodes;
+  int64_t n_elem;
+  const int32_t* conn;   // [E][10]
+  const T* xyz;          // [N][3]
+  const T* mat;          // [E][2]  (E, nu)
+  const uint8_t* nmask;  // [N]     bit c set <=> DOF c of the node is free
+};
+
+// Tiles of elements for the shared-memory accumulation kernel.
+struct Tiling {
+  int tile_elems = 0;     // elements per tile (last tile may be shorter)
+  int max_nodes = 0;      // largest node count of a tile
+  int64_t n_tiles = 0;
+  DevBuf node_ptr;        // int32 [n_tiles+1] offsets into node_ids
+  DevBuf node_ids;        // int32 [sum of tile node counts] global node ids per tile
+  DevBuf node_own;        // uint8, parallel to node_ids: 1 if this is the node's first tile
+  DevBuf lconn;           // uint16 [E][10] tile-local node index per element corner
+};
+
+struct SolverWork;  // defined in fe_solver.cu
+
+}  // namespace fe
+
+struct fe_mesh {
+  int device = 0;
+  int64_t n_nodes = 0;
+  int64_t n_elem = 0;
+  fe::DevBuf conn;      // int32 [E][10]
+  fe::DevBuf xyz64;     // double [N][3]
+  fe::DevBuf xyz32;     // float [N][3]
+  fe::DevBuf mat64;     // double [E][2]
+  fe::DevBuf mat32;     // float [E][2]
+  fe::DevBuf nmask;     // uint8 [N]
+  std::vector<double> young_host;
+  std::vector<double> poisson_host;
+  // 3x3 block Jacobi (built lazily, invalidated when materials change)
+  bool jacobi_ready = false;
+  fe::DevBuf binv64;    // double [N][9]
+  fe::DevBuf binv32;    // float [N][9]
+  // element tilings for the shared-memory EBE kernel, by elements per tile (built lazily)
+  std::map<int, std::unique_ptr<fe::Tiling>> tilings;
+  // EBE kernel per precision (0 = FP64, 1 = FP32) and R: -1 = default,
+  // 0 = direct, > 0 = tiled with that many elements per tile
+  int16_t variant[2][65];
+  // internal element order -> caller's element id (elements are stored in a
+  // locality-preserving order)
+  std::vector<int64_t> perm_host;
+  fe::DevBuf perm;      // int64 [E]
+  fe::DevBuf own_elem;  // uint16 [E]: bit a set if element e is the first element holding its node a
+  std::vector<int32_t> conn_host;  // [E][10] in internal order
+  // solver workspace (allocated lazily per R)
+  fe::SolverWork* work = nullptr;
+
+  template <typename T>
+  fe::MeshView<T> view() const;
+};
+
+namespace fe {
+
+// EBE product dispatch (fe_ebe.cu). x, y: device [N][R][3] of T.
+// If `skip` is non-NULL, every launched kernel returns at once when *skip != 0
+// (used for inner-loop steps after the stop test fired inside a CUDA graph).
+template <typename T>
+void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip = nullptr);
+
+// kernel choice: 0 = direct, > 0 = tiled with that tile size
+int ebe_get_variant(const fe_mesh* m, int R, int is_f32);
+void ebe_set_variant(fe_mesh* m, int R, int is_f32, int variant);
+const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
+// largest tile (elements) whose shared-memory footprint fits for (R, precision)
+bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32);
+
+// Block Jacobi (fe_solver.cu)
+void build_block_jacobi(fe_mesh* m, cudaStream_t s);
+
+// Adjoint (fe_adjoint.cu)
+void adjoint_grad(const fe_mesh* m, int R, const double* u, const double* lam, double* g, cudaStream_t s);
+
+void free_solver_work(fe_mesh* m);
+
+}  // namespace fe

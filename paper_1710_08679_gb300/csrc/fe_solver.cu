@@ -1,0 +1,990 @@
+// Solvers of K_bc u_r = f_r for R cases at once.
+//
+//  * FE_SOLVER_PCG64: CG with 3x3 block Jacobi in FP64 (the paper's PCGE
+//    reference solver of Sec. 4, Algorithm 1(a) without lines 8-17).
+//  * FE_SOLVER_FCG_MIXED: Algorithm 1 with the inner loop at level 0 only: an
+//    FP64 flexible (adaptive) CG whose preconditioner z = K^-1 r is an FP32
+//    block-Jacobi CG (Algorithm 1(b)) stopped at N steps or when
+//    max_r ||e_r||^2/||rbar_r||^2 <= eps (the max-over-cases rule of Sec. 3.1).
+//
+// GPU design: every per-case scalar (rho, gamma, alpha, beta, norms, masks)
+// lives in device arrays of length R; kernels read them directly, so one outer
+// iteration (including all N inner steps) runs without host round trips and is
+// captured once as a CUDA graph and replayed. Inner steps after the inner stop
+// test fires become no-ops (each kernel checks a device flag). Each case is
+// masked on its own once it converges. Vectors are [N][R][3]; a vector kernel's
+// thread handles one (node, case) pair and neighbouring threads touch
+// neighbouring addresses. Dot products accumulate per thread (FP32 products in
+// FP32 for the inner loop, FP64 otherwise), then per block in FP64 shared
+// memory, then with one FP64 atomic add per block and case.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fe_element.cuh"
+#include "fe_internal.cuh"
+
+namespace fe {
+
+// ---------------------------------------------------------------------------
+// per-case device state
+// ---------------------------------------------------------------------------
+enum DField {
+  D_FN2 = 0, D_RN2, D_RHO, D_GAM, D_ZQ, D_PQP, D_RHOP, D_ALPHA, D_BETA,
+  D_RBN2, D_EN2, D_RHOA, D_RHOB, D_GAMI, D_ALPHAI, D_BETAI, D_RT2, D_RELRES, D_COUNT
+};
+enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INNER, I_COUNT };
+
+struct Cases {
+  double* d;      // [D_COUNT][R]
+  int* i;         // [I_COUNT][R]
+  int* done;      // inner-loop stop flag (1 int)
+  int R;
+  __device__ __forceinline__ double& D(int f, int r) const { return d[f * R + r]; }
+  __device__ __forceinline__ int& I(int f, int r) const { return i[f * R + r]; }
+};
+
+struct SolverWork {
+  int R = 0;
+  int64_t N = 0;
+  DevBuf r, p, q;                 // double [N][R][3]
+  DevBuf rb, ub, eb, pb, qb;      // float  [N][R][3]
+  DevBuf tu, tq;                  // double [N][3] (single-case true residual)
+  DevBuf d, i;                    // case state
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  ~SolverWork() {
+    if (ev) cudaEventDestroy(ev);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+void free_solver_work(fe_mesh* m) {
+  delete m->work;
+  m->work = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// launch geometry for [N][R][3] vector kernels: blocks of K*R threads, thread
+// (j, r) = (threadIdx.x / R, threadIdx.x % R) handles node n = block*K + j
+// (grid-stride) and case r. K is the largest power of two with K*R <= 256.
+// ---------------------------------------------------------------------------
+struct VGeom {
+  int R, K, tpb;
+  unsigned grid;
+};
+
+static VGeom vgeom(int64_t N, int R, int sms) {
+  VGeom g;
+  g.R = R;
+  g.K = 1;
+  while (g.K * 2 * R <= 256) g.K *= 2;
+  g.tpb = g.K * R;
+  const int64_t need = (N + g.K - 1) / g.K;
+  const int64_t cap = (int64_t)sms * 8;
+  g.grid = (unsigned)(need < cap ? need : cap);
+  return g;
+}
+
+// sums v over the K threads of each case in the block and adds the block total
+// to out[r] (FP64 atomics). Every thread of the block must call it.
+__device__ __forceinline__ void reduce_cases(double v, int R, int K, double* sm, double* out) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  const int j = threadIdx.x / R;
+  for (int s = K >> 1; s > 0; s >>= 1) {
+    if (j < s) sm[threadIdx.x] += sm[threadIdx.x + s * R];
+    __syncthreads();
+  }
+  if (j == 0) atomicAdd(out + threadIdx.x, sm[threadIdx.x]);
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void mv3(const T* __restrict__ Mi, const T v[3], T z[3]) {
+  z[0] = Mi[0] * v[0] + Mi[1] * v[1] + Mi[2] * v[2];
+  z[1] = Mi[3] * v[0] + Mi[4] * v[1] + Mi[5] * v[2];
+  z[2] = Mi[6] * v[0] + Mi[7] * v[1] + Mi[8] * v[2];
+}
+
+#define VEC_LOOP_BEGIN                                    \
+  const int R = C.R;                                      \
+  const int r = threadIdx.x % R;                          \
+  const int K = blockDim.x / R;                           \
+  const int64_t stride = (int64_t)gridDim.x * K;          \
+  for (int64_t n = (int64_t)blockIdx.x * K + threadIdx.x / R; n < N; n += stride) { \
+    const int64_t o = (n * R + r) * 3;
+
+#define VEC_LOOP_END }
+
+// ---------------------------------------------------------------------------
+// block Jacobi: diagonal 3x3 blocks of K from the element closed form
+//   B_aa = (lam + mu) G_a + mu tr(G_a) I,  G_a = int grad N_a (x) grad N_a dV,
+//   corner: G_a = (3V/5) g_a g_a^T,
+//   edge kl: G = (8V/5)(g_k g_k^T + g_l g_l^T) + (4V/5)(g_k g_l^T + g_l g_k^T),
+// summed over elements, masked (constrained rows/columns -> identity), inverted.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void add_block(double* D, const double G[3][3], double lam, double mu) {
+  const double tr = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) atomicAdd(D + 3 * i + j, (lam + mu) * G[i][j] + (i == j ? mu * tr : 0.0));
+}
+
+__global__ void jacobi_diag_kernel(MeshView<double> M, double* __restrict__ Dg) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M.n_elem) return;
+  int nd[10];
+  for (int a = 0; a < 10; ++a) nd[a] = M.conn[10 * e + a];
+  double xc[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 3; ++i) xc[k][i] = M.xyz[3 * (int64_t)nd[k] + i];
+  ElemGeo<double> G;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], M.mat[2 * e], M.mat[2 * e + 1], G);
+  const double V = 20.0 * G.c;
+  for (int a = 0; a < 4; ++a) {
+    double Ga[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ga[i][j] = 0.6 * V * G.g[a][i] * G.g[a][j];
+    add_block(Dg + 9 * (int64_t)nd[a], Ga, G.lam, G.mu);
+  }
+  const int EK[6] = {0, 1, 0, 0, 1, 2}, EL[6] = {1, 2, 2, 3, 3, 3};
+  for (int q = 0; q < 6; ++q) {
+    const int k = EK[q], l = EL[q];
+    double Ga[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Ga[i][j] = 1.6 * V * (G.g[k][i] * G.g[k][j] + G.g[l][i] * G.g[l][j]) +
+                   0.8 * V * (G.g[k][i] * G.g[l][j] + G.g[l][i] * G.g[k][j]);
+    add_block(Dg + 9 * (int64_t)nd[edge_node(k, l)], Ga, G.lam, G.mu);
+  }
+}
+
+__global__ void jacobi_invert_kernel(int64_t N, const uint8_t* __restrict__ nmask, const double* __restrict__ Dg,
+                                     double* __restrict__ B64, float* __restrict__ B32, int* __restrict__ bad) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int mk = nmask[n];
+  double A[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const bool fi = (mk >> i) & 1, fj = (mk >> j) & 1;
+      A[i][j] = (fi && fj) ? Dg[9 * n + 3 * i + j] : (i == j ? 1.0 : 0.0);
+    }
+  const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+  if (!(det > 0.0) || !isfinite(det)) {
+    atomicExch(bad, 1);
+    for (int k = 0; k < 9; ++k) {
+      B64[9 * n + k] = (k % 4 == 0) ? 1.0 : 0.0;
+      B32[9 * n + k] = (k % 4 == 0) ? 1.f : 0.f;
+    }
+    return;
+  }
+  const double id = 1.0 / det;
+  double I[9];
+  I[0] = c00 * id;
+  I[1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id;
+  I[2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id;
+  I[3] = c01 * id;
+  I[4] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id;
+  I[5] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id;
+  I[6] = c02 * id;
+  I[7] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id;
+  I[8] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id;
+  for (int k = 0; k < 9; ++k) {
+    B64[9 * n + k] = I[k];
+    B32[9 * n + k] = (float)I[k];
+  }
+}
+
+void build_block_jacobi(fe_mesh* m, cudaStream_t s) {
+  if (m->jacobi_ready) return;
+  const int64_t N = m->n_nodes, E = m->n_elem;
+  DevBuf D, bad;
+  D.alloc((size_t)N * 9 * sizeof(double));
+  bad.alloc(sizeof(int));
+  if (!m->binv64.ptr) m->binv64.alloc((size_t)N * 9 * sizeof(double));
+  if (!m->binv32.ptr) m->binv32.alloc((size_t)N * 9 * sizeof(float));
+  FE_CUDA(cudaMemsetAsync(D.ptr, 0, D.bytes, s));
+  FE_CUDA(cudaMemsetAsync(bad.ptr, 0, sizeof(int), s));
+  jacobi_diag_kernel<<<(unsigned)((E + 127) / 128), 128, 0, s>>>(m->view<double>(), D.as<double>());
+  FE_CHECK_LAUNCH();
+  jacobi_invert_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, m->nmask.as<uint8_t>(), D.as<double>(),
+                                                                   m->binv64.as<double>(), m->binv32.as<float>(),
+                                                                   bad.as<int>());
+  FE_CHECK_LAUNCH();
+  int hbad = 0;
+  FE_CUDA(cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  FE_REQUIRE(hbad == 0, "block Jacobi: a free node has a singular or indefinite diagonal block "
+                        "(node touched by no element, or a degenerate material)");
+  m->jacobi_ready = true;
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels (N nodes, R cases; blockDim = K*R)
+// ---------------------------------------------------------------------------
+
+// u <- P u ; fn2 += ||P f||^2
+__global__ void k_prepare(int64_t N, Cases C, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
+                          double* __restrict__ u) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  const int mk = nmask[n];
+  for (int c = 0; c < 3; ++c) {
+    const bool fr = (mk >> c) & 1;
+    const double fv = fr ? f[o + c] : 0.0;
+    acc += fv * fv;
+    if (!fr) u[o + c] = 0.0;
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_FN2 * C.R);
+}
+
+// r = P f - q ; rn2 += ||r||^2
+__global__ void k_residual(int64_t N, Cases C, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
+                           const double* __restrict__ q, double* __restrict__ rv) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  const int mk = nmask[n];
+  for (int c = 0; c < 3; ++c) {
+    const double v = ((mk >> c) & 1) ? f[o + c] - q[o + c] : 0.0;
+    rv[o + c] = v;
+    acc += v * v;
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RN2 * C.R);
+}
+
+// PCG start: p = M^-1 r ; rho += (p, r)
+__global__ void k_pcg_init(int64_t N, Cases C, const double* __restrict__ Bi, const double* __restrict__ rv,
+                           double* __restrict__ p) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  double v[3] = {rv[o], rv[o + 1], rv[o + 2]}, z[3];
+  mv3(Bi + 9 * n, v, z);
+  for (int c = 0; c < 3; ++c) {
+    p[o + c] = z[c];
+    acc += z[c] * v[c];
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RHO * C.R);
+}
+
+// PCG restart of the cases flagged RESTART (their r was replaced by the true
+// residual): p = M^-1 r, rhoa += (M^-1 r, r) for those cases only
+__global__ void k_pcg_restart(int64_t N, Cases C, const double* __restrict__ Bi, const double* __restrict__ rv,
+                              double* __restrict__ p) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  if (C.I(I_RESTART, r)) {
+    double v[3] = {rv[o], rv[o + 1], rv[o + 2]}, z[3];
+    mv3(Bi + 9 * n, v, z);
+    for (int c = 0; c < 3; ++c) {
+      p[o + c] = z[c];
+      acc += z[c] * v[c];
+    }
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RHOA * C.R);
+}
+
+// u_r = 0 for cases whose right-hand side is zero
+__global__ void k_zero_trivial(int64_t N, Cases C, double* __restrict__ u) {
+  VEC_LOOP_BEGIN
+  if (!(C.D(D_FN2, r) > 0.0))
+    for (int c = 0; c < 3; ++c) u[o + c] = 0.0;
+  VEC_LOOP_END
+}
+
+// acc[field] += (a, b), inner loop (FP32) or outer (FP64); skipped when *skip
+template <typename T>
+__global__ void k_dot(int64_t N, Cases C, int field, const int* __restrict__ skip, const T* __restrict__ a,
+                      const T* __restrict__ b) {
+  extern __shared__ double sm[];
+  if (skip && *skip) return;
+  T acc = T(0);
+  VEC_LOOP_BEGIN
+  acc += a[o] * b[o] + a[o + 1] * b[o + 1] + a[o + 2] * b[o + 2];
+  VEC_LOOP_END
+  reduce_cases((double)acc, C.R, blockDim.x / C.R, sm, C.d + field * C.R);
+}
+
+// PCG update: u += a p ; r -= a q ; rhoa += (M^-1 r, r) ; rn2 += (r, r)
+__global__ void k_pcg_update(int64_t N, Cases C, const double* __restrict__ Bi, double* __restrict__ u,
+                             const double* __restrict__ p, double* __restrict__ rv, const double* __restrict__ q) {
+  extern __shared__ double sm[];
+  double a1 = 0.0, a2 = 0.0;
+  VEC_LOOP_BEGIN
+  if (C.I(I_ACTIVE, r)) {
+    const double al = C.D(D_ALPHA, r);
+    double v[3], z[3];
+    for (int c = 0; c < 3; ++c) {
+      u[o + c] += al * p[o + c];
+      v[c] = rv[o + c] - al * q[o + c];
+      rv[o + c] = v[c];
+    }
+    mv3(Bi + 9 * n, v, z);
+    a1 += z[0] * v[0] + z[1] * v[1] + z[2] * v[2];
+    a2 += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  }
+  VEC_LOOP_END
+  reduce_cases(a1, C.R, blockDim.x / C.R, sm, C.d + D_RHOA * C.R);
+  reduce_cases(a2, C.R, blockDim.x / C.R, sm, C.d + D_RN2 * C.R);
+}
+
+// PCG direction: p = M^-1 r + beta p (restarted cases: beta = 0)
+__global__ void k_pcg_p(int64_t N, Cases C, const double* __restrict__ Bi, const double* __restrict__ rv,
+                        double* __restrict__ p) {
+  VEC_LOOP_BEGIN
+  if (C.I(I_ACTIVE, r)) {
+    const double be = C.D(D_BETA, r);
+    double v[3] = {rv[o], rv[o + 1], rv[o + 2]}, z[3];
+    mv3(Bi + 9 * n, v, z);
+    for (int c = 0; c < 3; ++c) p[o + c] = z[c] + be * p[o + c];
+  }
+  VEC_LOOP_END
+}
+
+// FCG inner start (Alg. 1(a) lines 9-10): rbar = (float) r ; ubar = Mbar^-1 rbar ;
+// rbn2 += ||rbar||^2. Inactive cases get zeros.
+__global__ void k_cast_start(int64_t N, Cases C, const float* __restrict__ Bi, const double* __restrict__ rv,
+                             float* __restrict__ rb, float* __restrict__ ub) {
+  extern __shared__ double sm[];
+  float acc = 0.f;
+  VEC_LOOP_BEGIN
+  const bool act = C.I(I_ACTIVE, r);
+  float v[3], z[3];
+  for (int c = 0; c < 3; ++c) v[c] = act ? (float)rv[o + c] : 0.f;
+  mv3(Bi + 9 * n, v, z);
+  for (int c = 0; c < 3; ++c) {
+    rb[o + c] = v[c];
+    ub[o + c] = z[c];
+    acc += v[c] * v[c];
+  }
+  VEC_LOOP_END
+  reduce_cases((double)acc, C.R, blockDim.x / C.R, sm, C.d + D_RBN2 * C.R);
+}
+
+// Alg. 1(b) lines 1-2: e = rbar - Kbar ubar (q holds Kbar ubar); en2 += ||e||^2 ;
+// rhoa += (Mbar^-1 e, e)
+__global__ void k_inner_resid(int64_t N, Cases C, const float* __restrict__ Bi, const float* __restrict__ rb,
+                              const float* __restrict__ qb, float* __restrict__ eb) {
+  extern __shared__ double sm[];
+  float a1 = 0.f, a2 = 0.f;
+  VEC_LOOP_BEGIN
+  float v[3], z[3];
+  for (int c = 0; c < 3; ++c) {
+    v[c] = rb[o + c] - qb[o + c];
+    eb[o + c] = v[c];
+  }
+  mv3(Bi + 9 * n, v, z);
+  a1 += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  a2 += z[0] * v[0] + z[1] * v[1] + z[2] * v[2];
+  VEC_LOOP_END
+  reduce_cases((double)a1, C.R, blockDim.x / C.R, sm, C.d + D_EN2 * C.R);
+  reduce_cases((double)a2, C.R, blockDim.x / C.R, sm, C.d + D_RHOA * C.R);
+}
+
+// Alg. 1(b) lines 6-11: pbar = Mbar^-1 e + beta pbar
+__global__ void k_inner_p(int64_t N, Cases C, const float* __restrict__ Bi, const float* __restrict__ eb,
+                          float* __restrict__ pb) {
+  if (*C.done) return;
+  VEC_LOOP_BEGIN
+  const float be = (float)C.D(D_BETAI, r);
+  float v[3] = {eb[o], eb[o + 1], eb[o + 2]}, z[3];
+  mv3(Bi + 9 * n, v, z);
+  // the first step (beta = 0) must not read pbar: it holds the previous solve's data
+  if (be != 0.f)
+    for (int c = 0; c < 3; ++c) pb[o + c] = z[c] + be * pb[o + c];
+  else
+    for (int c = 0; c < 3; ++c) pb[o + c] = z[c];
+  VEC_LOOP_END
+}
+
+// Alg. 1(b) lines 16-17: e -= alpha q ; ubar += alpha p ; then en2, rhoa for the next step
+__global__ void k_inner_update(int64_t N, Cases C, const float* __restrict__ Bi, float* __restrict__ eb,
+                               const float* __restrict__ qb, float* __restrict__ ub, const float* __restrict__ pb) {
+  extern __shared__ double sm[];
+  if (*C.done) return;
+  float a1 = 0.f, a2 = 0.f;
+  VEC_LOOP_BEGIN
+  const float al = (float)C.D(D_ALPHAI, r);
+  float v[3], z[3];
+  for (int c = 0; c < 3; ++c) {
+    v[c] = eb[o + c] - al * qb[o + c];
+    eb[o + c] = v[c];
+    ub[o + c] += al * pb[o + c];
+  }
+  mv3(Bi + 9 * n, v, z);
+  a1 += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  a2 += z[0] * v[0] + z[1] * v[1] + z[2] * v[2];
+  VEC_LOOP_END
+  reduce_cases((double)a1, C.R, blockDim.x / C.R, sm, C.d + D_EN2 * C.R);
+  reduce_cases((double)a2, C.R, blockDim.x / C.R, sm, C.d + D_RHOA * C.R);
+}
+
+// zq += ((double) ubar, q_prev)
+__global__ void k_outer_zq(int64_t N, Cases C, const float* __restrict__ ub, const double* __restrict__ q) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  acc += (double)ub[o] * q[o] + (double)ub[o + 1] * q[o + 1] + (double)ub[o + 2] * q[o + 2];
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_ZQ * C.R);
+}
+
+// Alg. 1(a) line 23: p = z + beta p with z = (double) ubar
+__global__ void k_outer_p(int64_t N, Cases C, const float* __restrict__ ub, double* __restrict__ p) {
+  VEC_LOOP_BEGIN
+  if (C.I(I_ACTIVE, r)) {
+    const double be = C.D(D_BETA, r);
+    if (be != 0.0)
+      for (int c = 0; c < 3; ++c) p[o + c] = (double)ub[o + c] + be * p[o + c];
+    else
+      for (int c = 0; c < 3; ++c) p[o + c] = (double)ub[o + c];
+  }
+  VEC_LOOP_END
+}
+
+// Alg. 1(a) lines 25-26: rho += (z, r) ; gam += (p, q)
+__global__ void k_outer_dots(int64_t N, Cases C, const float* __restrict__ ub, const double* __restrict__ rv,
+                             const double* __restrict__ p, const double* __restrict__ q) {
+  extern __shared__ double sm[];
+  double a1 = 0.0, a2 = 0.0;
+  VEC_LOOP_BEGIN
+  for (int c = 0; c < 3; ++c) {
+    a1 += (double)ub[o + c] * rv[o + c];
+    a2 += p[o + c] * q[o + c];
+  }
+  VEC_LOOP_END
+  reduce_cases(a1, C.R, blockDim.x / C.R, sm, C.d + D_RHO * C.R);
+  reduce_cases(a2, C.R, blockDim.x / C.R, sm, C.d + D_GAM * C.R);
+}
+
+// Alg. 1(a) lines 28-29: r -= alpha q ; u += alpha p ; rn2 += ||r||^2
+__global__ void k_outer_update(int64_t N, Cases C, double* __restrict__ rv, const double* __restrict__ q,
+                               double* __restrict__ u, const double* __restrict__ p) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  if (C.I(I_ACTIVE, r)) {
+    const double al = C.D(D_ALPHA, r);
+    for (int c = 0; c < 3; ++c) {
+      const double v = rv[o + c] - al * q[o + c];
+      rv[o + c] = v;
+      u[o + c] += al * p[o + c];
+      acc += v * v;
+    }
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RN2 * C.R);
+}
+
+// single-case helpers for the true-residual confirmation
+__global__ void k_gather_case(int64_t N, int R, int c, const double* __restrict__ u, double* __restrict__ t) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  for (int k = 0; k < 3; ++k) t[3 * n + k] = u[(n * R + c) * 3 + k];
+}
+
+// rt2[c] = ||P f_c - t||^2 ; if `write_r`, r_c = P f_c - t
+__global__ void k_case_resid(int64_t N, int R, int c, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
+                             const double* __restrict__ t, double* __restrict__ rv, int write_r,
+                             double* __restrict__ out) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const int mk = nmask[n];
+    for (int k = 0; k < 3; ++k) {
+      const double v = ((mk >> k) & 1) ? f[(n * R + c) * 3 + k] - t[3 * n + k] : 0.0;
+      if (write_r) rv[(n * R + c) * 3 + k] = v;
+      acc += v * v;
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, sm[0]);
+}
+
+// ---------------------------------------------------------------------------
+// per-case scalar kernels (one block of R threads)
+// ---------------------------------------------------------------------------
+__global__ void s_init(Cases C) {
+  const int r = threadIdx.x;
+  for (int f = 0; f < D_COUNT; ++f) C.D(f, r) = 0.0;
+  for (int f = 0; f < I_COUNT; ++f) C.I(f, r) = 0;
+  C.I(I_FIRST, r) = 1;
+  if (r == 0) *C.done = 0;
+}
+
+// after ||f||^2 and ||r||^2: cases with f = 0 are finished (u = 0); others start
+__global__ void s_start(Cases C, double tol, int reset_u_for_zero_f) {
+  const int r = threadIdx.x;
+  const double fn2 = C.D(D_FN2, r);
+  const bool zero = !(fn2 > 0.0);
+  C.I(I_ACTIVE, r) = zero ? 0 : 1;
+  C.I(I_STATUS, r) = FE_OK;
+  C.D(D_RELRES, r) = zero ? 0.0 : sqrt(C.D(D_RN2, r) / fn2);
+  if (!zero && C.D(D_RN2, r) <= tol * tol * fn2) {
+    C.I(I_ACTIVE, r) = 0;   // the initial guess already meets the tolerance: confirm on the host
+    C.I(I_CAND, r) = 1;
+  }
+  (void)reset_u_for_zero_f;
+}
+
+__global__ void s_pcg_restart(Cases C) {
+  const int r = threadIdx.x;
+  if (C.I(I_RESTART, r)) {
+    C.D(D_RHO, r) = C.D(D_RHOA, r);
+    C.I(I_RESTART, r) = 0;
+  }
+  C.D(D_RHOA, r) = 0.0;
+}
+
+// PCG: alpha = rho / (p, q)
+__global__ void s_pcg_alpha(Cases C) {
+  const int r = threadIdx.x;
+  const double g = C.D(D_GAM, r);
+  C.D(D_GAM, r) = 0.0;
+  C.D(D_RHOA, r) = 0.0;
+  C.D(D_RN2, r) = 0.0;
+  if (!C.I(I_ACTIVE, r)) {
+    C.D(D_ALPHA, r) = 0.0;
+    return;
+  }
+  const double rho = C.D(D_RHO, r);
+  if (!(g > 0.0) || !isfinite(g) || !isfinite(rho)) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_EBREAKDOWN;
+    C.D(D_ALPHA, r) = 0.0;
+    return;
+  }
+  C.D(D_ALPHA, r) = rho / g;
+}
+
+// PCG: beta = rho_new / rho, convergence and iteration cap
+__global__ void s_pcg_beta(Cases C, double tol, int max_it) {
+  const int r = threadIdx.x;
+  if (!C.I(I_ACTIVE, r)) {
+    C.D(D_BETA, r) = 0.0;
+    return;
+  }
+  const double rn = C.D(D_RHOA, r);
+  C.D(D_BETA, r) = rn / C.D(D_RHO, r);
+  C.D(D_RHO, r) = rn;
+  C.I(I_OUTER, r) += 1;
+  const double rn2 = C.D(D_RN2, r), fn2 = C.D(D_FN2, r);
+  if (!isfinite(rn2)) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_EBREAKDOWN;
+  } else if (rn2 <= tol * tol * fn2) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_CAND, r) = 1;
+  } else if (C.I(I_OUTER, r) >= max_it) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_ENOCONV;
+  }
+}
+
+// FCG: start of one outer iteration
+__global__ void s_outer_begin(Cases C) {
+  const int r = threadIdx.x;
+  C.D(D_RBN2, r) = 0.0;
+  C.D(D_EN2, r) = 0.0;
+  C.D(D_RHOA, r) = 0.0;
+  C.D(D_ZQ, r) = 0.0;
+  if (r == 0) *C.done = 0;
+}
+
+// inner stop test before step `step` and inner beta (Alg. 1(b) lines 5, 8-10)
+__global__ void s_inner_check(Cases C, int step, int n_inner, double eps) {
+  __shared__ int go;
+  const int r = threadIdx.x;
+  if (r == 0) go = 0;
+  __syncthreads();
+  if (*C.done) return;
+  const double rb = C.D(D_RBN2, r);
+  const bool act = C.I(I_ACTIVE, r) && rb > 0.0;
+  const double ratio = C.D(D_EN2, r) / rb;
+  if (act && !(ratio <= eps)) atomicOr(&go, 1);   // NaN counts as "not converged"
+  __syncthreads();
+  if (r == 0 && (!go || step >= n_inner)) *C.done = 1;
+  const double rhob = C.D(D_RHOB, r);
+  C.D(D_BETAI, r) = (step > 0 && rhob != 0.0 && act) ? C.D(D_RHOA, r) / rhob : 0.0;
+  C.D(D_GAMI, r) = 0.0;
+}
+
+// inner alpha (Alg. 1(b) lines 13-15)
+__global__ void s_inner_alpha(Cases C) {
+  const int r = threadIdx.x;
+  if (*C.done) return;
+  const double g = C.D(D_GAMI, r), rho = C.D(D_RHOA, r);
+  const bool ok = C.I(I_ACTIVE, r) && C.D(D_RBN2, r) > 0.0 && g > 0.0 && isfinite(g) && isfinite(rho);
+  C.D(D_ALPHAI, r) = ok ? rho / g : 0.0;
+  C.D(D_RHOB, r) = rho;
+  C.D(D_EN2, r) = 0.0;
+  C.D(D_RHOA, r) = 0.0;
+  if (C.I(I_ACTIVE, r)) C.I(I_INNER, r) += 1;
+}
+
+// outer beta (Alg. 1(a) lines 19-22, read as flexible CG unless literal)
+__global__ void s_outer_beta(Cases C, int literal) {
+  const int r = threadIdx.x;
+  double be = 0.0;
+  if (C.I(I_ACTIVE, r) && !C.I(I_FIRST, r) && !C.I(I_RESTART, r)) {
+    const double zq = C.D(D_ZQ, r);
+    be = literal ? zq / C.D(D_RHOP, r) : -zq / C.D(D_PQP, r);
+    if (!isfinite(be)) be = 0.0;
+  }
+  if (C.I(I_ACTIVE, r)) {
+    C.I(I_FIRST, r) = 0;
+    C.I(I_RESTART, r) = 0;
+  }
+  C.D(D_BETA, r) = be;
+  C.D(D_RHO, r) = 0.0;
+  C.D(D_GAM, r) = 0.0;
+}
+
+// outer alpha (Alg. 1(a) line 27) and bookkeeping
+__global__ void s_outer_alpha(Cases C) {
+  const int r = threadIdx.x;
+  C.D(D_RN2, r) = 0.0;
+  if (!C.I(I_ACTIVE, r)) {
+    C.D(D_ALPHA, r) = 0.0;
+    return;
+  }
+  const double g = C.D(D_GAM, r), rho = C.D(D_RHO, r);
+  if (!(g > 0.0) || !isfinite(g) || !isfinite(rho)) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_EBREAKDOWN;
+    C.D(D_ALPHA, r) = 0.0;
+    return;
+  }
+  C.D(D_ALPHA, r) = rho / g;
+  C.D(D_PQP, r) = g;
+  C.D(D_RHOP, r) = rho;
+  C.I(I_OUTER, r) += 1;
+}
+
+// outer stop test (Alg. 1(a) line 8, per case) and iteration cap
+__global__ void s_outer_check(Cases C, double tol, int max_outer) {
+  const int r = threadIdx.x;
+  if (!C.I(I_ACTIVE, r)) return;
+  const double rn2 = C.D(D_RN2, r), fn2 = C.D(D_FN2, r);
+  if (!isfinite(rn2)) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_EBREAKDOWN;
+  } else if (rn2 <= tol * tol * fn2) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_CAND, r) = 1;
+  } else if (C.I(I_OUTER, r) >= max_outer) {
+    C.I(I_ACTIVE, r) = 0;
+    C.I(I_STATUS, r) = FE_ENOCONV;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct Solve {
+  fe_mesh* m;
+  SolverWork* w;
+  int R;
+  int64_t N;
+  Cases C;
+  VGeom g;
+  size_t sm;  // shared bytes of reducing vector kernels
+  cudaStream_t s;
+  const double* f;
+  double* u;
+  fe_solve_opts o;
+
+  template <typename K, typename... A>
+  void vec(K kern, A... args) {
+    kern<<<g.grid, g.tpb, sm, s>>>(N, C, args...);
+    FE_CHECK_LAUNCH();
+  }
+  template <typename K, typename... A>
+  void scal(K kern, A... args) {
+    kern<<<1, R, 0, s>>>(C, args...);
+    FE_CHECK_LAUNCH();
+  }
+
+  // ||P f_c - K u_c|| / ||P f_c|| with an FP64 single-case product; if the
+  // tolerance is not met and `reset`, r_c is replaced by that true residual.
+  double true_relres(int c, double fn2, bool reset) {
+    k_gather_case<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, R, c, u, w->tu.as<double>());
+    FE_CHECK_LAUNCH();
+    ebe_apply<double>(m, 1, w->tu.as<double>(), w->tq.as<double>(), s);
+    double* out = w->d.as<double>() + D_RT2 * R + c;
+    FE_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+    k_case_resid<<<(unsigned)std::min<int64_t>((N + 255) / 256, 1024), 256, 0, s>>>(
+        N, R, c, m->nmask.as<uint8_t>(), f, w->tq.as<double>(), w->r.as<double>(), reset ? 1 : 0, out);
+    FE_CHECK_LAUNCH();
+    double rt2 = 0.0;
+    FE_CUDA(cudaMemcpyAsync(&rt2, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    return fn2 > 0.0 ? std::sqrt(rt2 / fn2) : 0.0;
+  }
+};
+
+static SolverWork* get_work(fe_mesh* m, int R) {
+  SolverWork* w = m->work;
+  if (w && w->R == R) return w;
+  free_solver_work(m);
+  w = new SolverWork();
+  m->work = w;
+  const int64_t N = m->n_nodes;
+  const size_t v = (size_t)N * R * 3;
+  w->R = R;
+  w->N = N;
+  w->r.alloc(v * 8);
+  w->p.alloc(v * 8);
+  w->q.alloc(v * 8);
+  w->rb.alloc(v * 4);
+  w->ub.alloc(v * 4);
+  w->eb.alloc(v * 4);
+  w->pb.alloc(v * 4);
+  w->qb.alloc(v * 4);
+  w->tu.alloc((size_t)N * 3 * 8);
+  w->tq.alloc((size_t)N * 3 * 8);
+  w->d.alloc((size_t)D_COUNT * R * 8 + 64);
+  w->i.alloc((size_t)I_COUNT * R * 4 + 64);
+  FE_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+  FE_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
+  return w;
+}
+
+// the FCG outer iteration (Alg. 1(a) lines 9-29 with lines 11-16 dropped)
+static void fcg_iteration(Solve& S) {
+  SolverWork* w = S.w;
+  fe_mesh* m = S.m;
+  const float* B32 = m->binv32.as<float>();
+  S.scal(s_outer_begin);
+  S.vec(k_cast_start, B32, w->r.as<double>(), w->rb.as<float>(), w->ub.as<float>());
+  ebe_apply<float>(m, S.R, w->ub.as<float>(), w->qb.as<float>(), S.s);
+  S.vec(k_inner_resid, B32, w->rb.as<float>(), w->qb.as<float>(), w->eb.as<float>());
+  for (int step = 0; step <= S.o.n_inner; ++step) {
+    S.scal(s_inner_check, step, S.o.n_inner, S.o.eps_inner);
+    if (step == S.o.n_inner) break;
+    S.vec(k_inner_p, B32, w->eb.as<float>(), w->pb.as<float>());
+    ebe_apply<float>(m, S.R, w->pb.as<float>(), w->qb.as<float>(), S.s, S.C.done);
+    S.vec(k_dot<float>, (int)D_GAMI, (const int*)S.C.done, (const float*)w->pb.as<float>(),
+          (const float*)w->qb.as<float>());
+    S.scal(s_inner_alpha);
+    S.vec(k_inner_update, B32, w->eb.as<float>(), w->qb.as<float>(), w->ub.as<float>(), w->pb.as<float>());
+  }
+  S.vec(k_outer_zq, (const float*)w->ub.as<float>(), (const double*)w->q.as<double>());
+  S.scal(s_outer_beta, S.o.literal_beta);
+  S.vec(k_outer_p, (const float*)w->ub.as<float>(), w->p.as<double>());
+  ebe_apply<double>(m, S.R, w->p.as<double>(), w->q.as<double>(), S.s);
+  S.vec(k_outer_dots, (const float*)w->ub.as<float>(), (const double*)w->r.as<double>(),
+        (const double*)w->p.as<double>(), (const double*)w->q.as<double>());
+  S.scal(s_outer_alpha);
+  S.vec(k_outer_update, w->r.as<double>(), (const double*)w->q.as<double>(), S.u, (const double*)w->p.as<double>());
+  S.scal(s_outer_check, S.o.tol, S.o.max_outer);
+}
+
+// one PCG iteration
+static void pcg_iteration(Solve& S) {
+  SolverWork* w = S.w;
+  const double* B64 = S.m->binv64.as<double>();
+  ebe_apply<double>(S.m, S.R, w->p.as<double>(), w->q.as<double>(), S.s);
+  S.vec(k_dot<double>, (int)D_GAM, (const int*)nullptr, (const double*)w->p.as<double>(),
+        (const double*)w->q.as<double>());
+  S.scal(s_pcg_alpha);
+  S.vec(k_pcg_update, B64, S.u, (const double*)w->p.as<double>(), w->r.as<double>(),
+        (const double*)w->q.as<double>());
+  S.scal(s_pcg_beta, S.o.tol, S.o.max_outer);
+  S.vec(k_pcg_p, B64, (const double*)w->r.as<double>(), w->p.as<double>());
+}
+
+static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const fe_solve_opts& o,
+                           fe_solve_stats* stats, cudaStream_t user) {
+  SolverWork* w = get_work(m, R);
+  cudaStream_t s = w->stream;
+  // order after the caller's pending work on `user`
+  FE_CUDA(cudaEventRecord(w->ev, user));
+  FE_CUDA(cudaStreamWaitEvent(s, w->ev, 0));
+  build_block_jacobi(m, s);
+  int sms = 0;
+  FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+  Solve S;
+  S.m = m;
+  S.w = w;
+  S.R = R;
+  S.N = m->n_nodes;
+  S.C = Cases{w->d.as<double>(), w->i.as<int>(), w->i.as<int>() + I_COUNT * R, R};
+  S.g = vgeom(S.N, R, sms);
+  S.sm = (size_t)S.g.tpb * sizeof(double);
+  S.s = s;
+  S.f = f;
+  S.u = u;
+  S.o = o;
+  const bool pcg = o.solver == FE_SOLVER_PCG64;
+
+  // start: u = P u, r = P f - K u, ||f||, ||r||
+  S.scal(s_init);
+  S.vec(k_prepare, m->nmask.as<uint8_t>(), f, u);
+  ebe_apply<double>(m, R, u, w->q.as<double>(), s);
+  S.vec(k_residual, m->nmask.as<uint8_t>(), f, (const double*)w->q.as<double>(), w->r.as<double>());
+  S.scal(s_start, o.tol, 0);
+  S.vec(k_zero_trivial, u);
+  FE_CUDA(cudaMemsetAsync(w->q.ptr, 0, w->q.bytes, s));
+  FE_CUDA(cudaMemsetAsync(w->p.ptr, 0, w->p.bytes, s));
+  FE_CUDA(cudaMemsetAsync(w->pb.ptr, 0, w->pb.bytes, s));
+  if (pcg) S.vec(k_pcg_init, m->binv64.as<double>(), (const double*)w->r.as<double>(), w->p.as<double>());
+
+  // capture one iteration as a graph
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graph) {
+    cudaGraph_t graph;
+    FE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      if (pcg) pcg_iteration(S); else fcg_iteration(S);
+    } catch (...) {
+      cudaStreamEndCapture(s, &graph);
+      throw;
+    }
+    FE_CUDA(cudaStreamEndCapture(s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FE_CUDA(e);
+  }
+
+  std::vector<int> hi((size_t)I_COUNT * R);
+  std::vector<double> hd((size_t)D_COUNT * R);
+  const int check = o.check_every < 1 ? 1 : o.check_every;
+  fe_status result = FE_OK;
+  try {
+    // the iteration loop: replay, then read the per-case flags every `check` iterations
+    for (int64_t it = 0;; ++it) {
+      FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
+      FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
+      FE_CUDA(cudaStreamSynchronize(s));
+      // confirm candidates with the true FP64 residual
+      bool any_active = false;
+      for (int c = 0; c < R; ++c) {
+        if (hi[I_CAND * R + c]) {
+          const double fn2 = hd[D_FN2 * R + c];
+          const double rel = S.true_relres(c, fn2, true);
+          int one = 1, zero = 0;
+          FE_CUDA(cudaMemcpyAsync(w->i.as<int>() + I_CAND * R + c, &zero, 4, cudaMemcpyHostToDevice, s));
+          if (rel <= o.tol) {
+            FE_CUDA(cudaMemcpyAsync(w->d.as<double>() + D_RELRES * R + c, &rel, 8, cudaMemcpyHostToDevice, s));
+          } else {
+            // recursive residual drifted from the true one: continue from the true residual
+            FE_CUDA(cudaMemcpyAsync(w->i.as<int>() + I_ACTIVE * R + c, &one, 4, cudaMemcpyHostToDevice, s));
+            FE_CUDA(cudaMemcpyAsync(w->i.as<int>() + I_RESTART * R + c, &one, 4, cudaMemcpyHostToDevice, s));
+            any_active = true;
+          }
+          FE_CUDA(cudaStreamSynchronize(s));
+        }
+        if (hi[I_ACTIVE * R + c]) any_active = true;
+      }
+      if (pcg) {
+        // cases whose recursive residual drifted restart CG from their true residual
+        FE_CUDA(cudaMemsetAsync(w->d.as<double>() + D_RHOA * R, 0, R * 8, s));
+        S.vec(k_pcg_restart, m->binv64.as<double>(), (const double*)w->r.as<double>(), w->p.as<double>());
+        S.scal(s_pcg_restart);
+      }
+      if (!any_active) break;
+      for (int k = 0; k < check; ++k) {
+        if (exec) {
+          FE_CUDA(cudaGraphLaunch(exec, s));
+        } else if (pcg) {
+          pcg_iteration(S);
+        } else {
+          fcg_iteration(S);
+        }
+      }
+    }
+    FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < R; ++c) {
+      int st = hi[I_STATUS * R + c];
+      double rel = hd[D_RELRES * R + c];
+      if (st != FE_OK) rel = S.true_relres(c, hd[D_FN2 * R + c], false);
+      if (stats) {
+        stats[c].outer_iters = hi[I_OUTER * R + c];
+        stats[c].inner_iters = hi[I_INNER * R + c];
+        stats[c].relres = rel;
+        stats[c].status = st;
+        stats[c].pad = 0;
+      }
+      if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
+      else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
+    }
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    throw;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  // the caller's stream continues after the solve
+  FE_CUDA(cudaEventRecord(w->ev, s));
+  FE_CUDA(cudaStreamWaitEvent(user, w->ev, 0));
+  if (result != FE_OK) set_error("fe_pcg_solve: %s", result == FE_EBREAKDOWN ? "breakdown in at least one case"
+                                                                            : "iteration cap reached in at least one case");
+  return result;
+}
+
+}  // namespace fe
+
+extern "C" fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* f, double* u,
+                                  const fe_solve_opts* opts, fe_solve_stats* stats, void* stream) {
+  try {
+    fe::clear_error();
+    FE_REQUIRE(mesh != nullptr, "mesh is NULL");
+    FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range [1, 64]", R);
+    FE_REQUIRE(f != nullptr && u != nullptr, "NULL vector");
+    fe_solve_opts o;
+    fe_solve_opts_default(&o);
+    if (opts) o = *opts;
+    FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED, "unknown solver %d", o.solver);
+    FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
+    FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
+    FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
+    FE_REQUIRE(o.eps_inner >= 0.0, "eps_inner must be >= 0");
+    fe_mesh* m = const_cast<fe_mesh*>(mesh);
+    fe::DeviceGuard dg(m->device);
+    return fe::run_solve(m, R, f, u, o, stats, (cudaStream_t)stream);
+  } catch (const fe::Failure& x) {
+    return x.status;
+  } catch (...) {
+    fe::set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}
+
+extern "C" fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void* stream) {
+  try {
+    fe::clear_error();
+    FE_REQUIRE(mesh != nullptr && binv_dev != nullptr, "NULL argument");
+    fe_mesh* m = const_cast<fe_mesh*>(mesh);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe::build_block_jacobi(m, s);
+    FE_CUDA(cudaMemcpyAsync(binv_dev, m->binv64.ptr, m->binv64.bytes, cudaMemcpyDeviceToDevice, s));
+    return FE_OK;
+  } catch (const fe::Failure& x) {
+    return x.status;
+  } catch (...) {
+    fe::set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}

@@ -1,0 +1,251 @@
+"""Thin Python binding of libfe (argument marshalling only).
+
+Every step of the computation runs in libfe's CUDA kernels; this module checks
+shapes and dtypes, passes raw pointers and the current CUDA stream, and turns
+fe_status codes into exceptions. There is no CPU fallback: if libfe.so is
+missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfe.so")
+
+FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT = range(7)
+FE_F64, FE_F32 = 0, 1
+FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED = 0, 1
+EBE_DIRECT, EBE_TILED = 0, 1
+
+STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
+                5: "FE_EBREAKDOWN", 6: "FE_ETIMEOUT"}
+
+# every symbol include/fe.h declares
+EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_create", "fe_mesh_destroy",
+            "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
+            "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_adjoint_grad"]
+
+
+class FeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int32), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
+                ("n_inner", ctypes.c_int32), ("eps_inner", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def load(path: Optional[str] = None):
+    """Load libfe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfe.so not found at {path}; build it with paper_1710_08679_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.fe_last_error.restype = ctypes.c_char_p
+    lib.fe_version.restype = ctypes.c_char_p
+    lib.fe_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+    lib.fe_solve_opts_default.restype = None
+    lib.fe_mesh_create.argtypes = [_i64, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(_vp)]
+    lib.fe_mesh_destroy.argtypes = [_vp]
+    lib.fe_mesh_destroy.restype = None
+    lib.fe_mesh_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    lib.fe_mesh_set_log_young.argtypes = [_vp, _vp, _vp]
+    lib.fe_ebe_apply.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    lib.fe_ebe_set_variant.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp]
+    lib.fe_ebe_get_variant.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+    lib.fe_ebe_tune.argtypes = [_vp, _i32, _i32, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+    lib.fe_pcg_solve.argtypes = [_vp, _i32, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp]
+    lib.fe_adjoint_grad.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
+    lib.fe_block_jacobi.argtypes = [_vp, _vp, _vp]
+    for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
+                 "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_adjoint_grad"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != FE_OK:
+        msg = load().fe_last_error().decode(errors="replace")
+        raise FeError(status, f"{what}: {msg}")
+
+
+def version() -> str:
+    return load().fe_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(device):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Device-resident TET10 mesh (libfe handle)."""
+
+    def __init__(self, coords, conn, young, poisson, free, device: int = 0):
+        lib = load()
+        self._coords = np.ascontiguousarray(coords, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        young = np.ascontiguousarray(young, dtype=np.float64)
+        poisson = np.ascontiguousarray(poisson, dtype=np.float64)
+        free = np.ascontiguousarray(free, dtype=np.uint8)
+        N, E = self._coords.shape[0], conn.shape[0]
+        if self._coords.shape != (N, 3) or conn.shape != (E, 10) or young.shape != (E,) or \
+                poisson.shape != (E,) or free.shape != (N, 3):
+            raise ValueError("mesh arrays have inconsistent shapes")
+        self.device = int(device)
+        torch = _torch()
+        h = ctypes.c_void_p()
+        st = lib.fe_mesh_create(N, self._coords.ctypes.data, E, conn.ctypes.data, young.ctypes.data,
+                                poisson.ctypes.data, free.ctypes.data, self.device,
+                                _stream_ptr(torch.device("cuda", self.device)), ctypes.byref(h))
+        _check(st, "fe_mesh_create")
+        self._h = h
+        self.n_nodes, self.n_elem = N, E
+        self.free = torch.from_numpy(free.astype(np.float64)).to(f"cuda:{self.device}")
+
+    @classmethod
+    def from_mesh(cls, m, device: int = 0) -> "Mesh":
+        return cls(m.coords, m.conn, m.young, m.poisson, m.free, device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fe_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_dof(self) -> int:
+        return 3 * self.n_nodes
+
+    def _stream(self):
+        return _stream_ptr(_torch().device("cuda", self.device))
+
+    # ---- operator -------------------------------------------------------
+    def ebe(self, x, out=None):
+        """y = K_bc x for x [N, R, 3] (float64 or float32 CUDA tensor)."""
+        torch = _torch()
+        if x.dim() != 3 or x.shape[0] != self.n_nodes or x.shape[2] != 3:
+            raise ValueError("x must be [N, R, 3]")
+        R = int(x.shape[1])
+        dt = {torch.float64: FE_F64, torch.float32: FE_F32}.get(x.dtype)
+        if dt is None:
+            raise TypeError("x must be float64 or float32")
+        xp = _dev_ptr(x, x.dtype, name="x")
+        y = torch.empty_like(x) if out is None else out
+        yp = _dev_ptr(y, x.dtype, x.shape, name="out")
+        _check(load().fe_ebe_apply(self._h, R, dt, xp, yp, self._stream()), "fe_ebe_apply")
+        return y
+
+    def set_variant(self, R: int, dtype, variant: int, tile_elems: int = 48):
+        dt = FE_F32 if dtype in ("f32", np.float32) or str(dtype).endswith("float32") else FE_F64
+        _check(load().fe_ebe_set_variant(self._h, int(R), dt, int(variant), int(tile_elems), self._stream()),
+               "fe_ebe_set_variant")
+
+    def get_variant(self, R: int, dtype):
+        dt = FE_F32 if dtype in ("f32", np.float32) or str(dtype).endswith("float32") else FE_F64
+        v, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fe_ebe_get_variant(self._h, int(R), dt, ctypes.byref(v), ctypes.byref(t)),
+               "fe_ebe_get_variant")
+        return v.value, t.value
+
+    def tune(self, R: int, dtype):
+        """Time the EBE variants for (R, dtype) on this mesh and keep the fastest."""
+        dt = FE_F32 if dtype in ("f32", np.float32) or str(dtype).endswith("float32") else FE_F64
+        v, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fe_ebe_tune(self._h, int(R), dt, self._stream(), ctypes.byref(v), ctypes.byref(t)),
+               "fe_ebe_tune")
+        return v.value, t.value
+
+    def set_log_young(self, logE):
+        torch = _torch()
+        p = _dev_ptr(logE, torch.float64, (self.n_elem,), name="logE")
+        _check(load().fe_mesh_set_log_young(self._h, p, self._stream()), "fe_mesh_set_log_young")
+
+    # ---- solvers --------------------------------------------------------
+    def solve(self, f, u0=None, solver: str = "fcg_mixed", tol: float = 1e-8, max_outer: int = 20000,
+              n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
+              check_every: int = 1, raise_on_fail: bool = True):
+        """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status)."""
+        torch = _torch()
+        R = int(f.shape[1])
+        fp = _dev_ptr(f, torch.float64, (self.n_nodes, R, 3), name="f")
+        u = torch.zeros_like(f) if u0 is None else u0.clone()
+        up = _dev_ptr(u, torch.float64, (self.n_nodes, R, 3), name="u")
+        o = SolveOpts()
+        load().fe_solve_opts_default(ctypes.byref(o))
+        o.solver = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED}[solver]
+        o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
+        o.use_graph, o.literal_beta, o.check_every = int(bool(use_graph)), int(bool(literal_beta)), int(check_every)
+        stats = (SolveStats * R)()
+        st = load().fe_pcg_solve(self._h, R, fp, up, ctypes.byref(o), stats, self._stream())
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, relres=s.relres, status=s.status) for s in stats]
+        if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
+            _check(st, "fe_pcg_solve")
+        return u, out, st
+
+    def block_jacobi(self):
+        """Inverse 3x3 diagonal blocks of K_bc, float64 [N, 3, 3]."""
+        torch = _torch()
+        out = torch.empty((self.n_nodes, 3, 3), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(load().fe_block_jacobi(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()), "fe_block_jacobi")
+        return out
+
+    def adjoint_grad(self, u, lam):
+        """g_e = -sum_r (P lam_r)_e^T K_e (P u_r)_e, float64 [E]."""
+        torch = _torch()
+        R = int(u.shape[1])
+        up = _dev_ptr(u, torch.float64, (self.n_nodes, R, 3), name="u")
+        lp = _dev_ptr(lam, torch.float64, (self.n_nodes, R, 3), name="lambda")
+        g = torch.empty(self.n_elem, dtype=torch.float64, device=u.device)
+        _check(load().fe_adjoint_grad(self._h, R, up, lp, ctypes.c_void_p(g.data_ptr()), self._stream()),
+               "fe_adjoint_grad")
+        return g

@@ -1,0 +1,146 @@
+"""GPU parity of the EBE product (fe_ebe_apply through the C ABI) against the
+CPU oracle's assembled CSR product.
+
+Bar: relative L2 error <= 1e-12 in FP64 and <= 2e-6 in FP32 (the FP32 input is
+the FP32-rounded x, and the oracle evaluates that same x in FP64).
+"""
+import numpy as np
+import pytest
+
+from _util import ensure_lib, rel_l2
+
+import oracle
+from paper_1710_08679_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+
+TOL64, TOL32 = 1e-12, 2e-6
+
+
+def gpu_mesh(m):
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    return fe.Mesh.from_mesh(m)
+
+
+def run(M, x, dtype, variant=None, tile=48):
+    """Product through the C ABI; for the tiled kernel, the largest tile <= `tile`
+    (halving) whose shared-memory footprint fits at this R and precision."""
+    from paper_1710_08679_gb300 import fe
+    t = torch.from_numpy(x).to("cuda", dtype=dtype)
+    if variant is not None:
+        while True:
+            try:
+                M.set_variant(x.shape[1], "f32" if dtype == torch.float32 else "f64", variant, tile)
+                break
+            except fe.FeError as exc:
+                if variant == 0 or tile <= 1 or "does not fit" not in str(exc):
+                    raise
+                tile //= 2
+    y = M.ebe(t)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+MESHES = {
+    "box1": lambda: mg.plain_box(n=1, jitter=0.0),
+    "box2": lambda: mg.plain_box(n=2, jitter=0.1, seed=4),
+    "ragged": lambda: mg.crust_block(shape=(5, 3, 4), h=1000.0, jitter=0.15, seed=2)[0],
+    "box8": lambda: mg.plain_box(),
+}
+
+
+@pytest.fixture(scope="module", params=list(MESHES))
+def mesh_pair(request):
+    m = MESHES[request.param]()
+    return m, oracle.assemble(m), gpu_mesh(m)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [1, 3, 4, 16, 32])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ebe_fp64_matches_oracle(mesh_pair, R, variant):
+    m, K, M = mesh_pair
+    x = mg.random_vectors(m.n_nodes, R, seed=100 + R)
+    y_ref = oracle.spmv(K, x)
+    y = run(M, x, torch.float64, variant, tile=48)
+    assert rel_l2(y, y_ref) <= TOL64
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [1, 3, 4, 16, 32])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ebe_fp32_matches_oracle(mesh_pair, R, variant):
+    m, K, M = mesh_pair
+    x = mg.random_vectors(m.n_nodes, R, seed=200 + R).astype(np.float32).astype(np.float64)
+    y_ref = oracle.spmv(K, x)
+    y = run(M, x, torch.float32, variant, tile=24)
+    assert rel_l2(y, y_ref) <= TOL32
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tile", [1, 7, 24, 96, 384])
+def test_tiled_tile_sizes_and_ragged_tail(tile):
+    m = MESHES["ragged"]()
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, 4, seed=9)
+    y = run(M, x, torch.float64, 1, tile=tile)
+    assert rel_l2(y, oracle.spmv(K, x)) <= TOL64
+    assert M.get_variant(4, "f64") == (1, tile)
+
+
+@pytest.mark.gpu
+def test_batched_equals_separate_products():
+    m = MESHES["box8"]()
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, 8, seed=5)
+    yb = run(M, x, torch.float64)
+    for r in (0, 3, 7):
+        ys = run(M, np.ascontiguousarray(x[:, r:r + 1]), torch.float64)
+        assert rel_l2(yb[:, r:r + 1], ys) <= 1e-14
+
+
+@pytest.mark.gpu
+def test_constrained_dofs_copy_input():
+    m = MESHES["box2"]()
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, 2, seed=6)
+    y = run(M, x, torch.float64)
+    fixed = m.free == 0
+    assert np.array_equal(y[:, 0][fixed], x[:, 0][fixed])
+    assert np.array_equal(y[:, 1][fixed], x[:, 1][fixed])
+
+
+@pytest.mark.gpu
+def test_autotuner_picks_a_valid_kernel():
+    m = MESHES["box8"]()
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    v, us = M.tune(16, "f32")
+    assert v >= 0 and us > 0
+    x = mg.random_vectors(m.n_nodes, 16, seed=7).astype(np.float32).astype(np.float64)
+    y = run(M, x, torch.float32)
+    assert rel_l2(y, oracle.spmv(K, x)) <= TOL32
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_crust_block_sampled_rows(dtype):
+    """The 70x70x35-hexahedra crust block (1,029,000 elements, 4,234,653 DOF) at
+    R = 16 in the kernel configuration the benchmark times (after tuning): rows
+    sampled across the mesh against the oracle's element-by-element row sums."""
+    m, _ = mg.crust_block()
+    M = gpu_mesh(m)
+    R = 16
+    x = mg.random_vectors(m.n_nodes, R, seed=100 + R)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    M.tune(R, dtype)
+    y = run(M, x, tdt)
+    rng = np.random.default_rng(0)
+    nodes = np.unique(np.concatenate([rng.integers(0, m.n_nodes, 3000), [0, m.n_nodes - 1]]))
+    ys = oracle.sampled_product(m, x, nodes)
+    assert rel_l2(y[nodes], ys) <= (TOL64 if dtype == "f64" else TOL32)

@@ -1,0 +1,176 @@
+"""GPU solver parity (fe_pcg_solve, fe_block_jacobi, fe_adjoint_grad through the
+C ABI) against the CPU oracle.
+
+Solutions are unique (K_bc is SPD) but iterates and atomic summation order are
+not, so the checks compare solutions, true residuals and iteration counts within
+a margin, never iterates.
+"""
+import numpy as np
+import pytest
+
+from _util import ensure_lib, rel_l2
+
+import oracle
+from paper_1710_08679_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+
+
+def gpu_mesh(m):
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    return fe.Mesh.from_mesh(m)
+
+
+@pytest.fixture(scope="module")
+def box8():
+    m = mg.plain_box()
+    K = oracle.assemble(m)
+    return m, K, gpu_mesh(m)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.gpu
+def test_block_jacobi_matches_oracle(box8):
+    m, K, M = box8
+    ref = oracle.block_jacobi(K)
+    got = M.block_jacobi().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.gpu
+def test_pcg64_plain_box(box8):
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    u, stats, st = M.solve(cuda(f), solver="pcg64", tol=1e-8)
+    assert st == 0 and stats[0]["status"] == 0
+    assert stats[0]["relres"] <= 1e-8
+    ud = oracle.direct_solve(K, f)
+    assert rel_l2(u.cpu().numpy(), ud) <= 1e-6
+    _, it, _ = oracle.pcg(K, f, tol=1e-8)
+    assert abs(stats[0]["outer"] - int(it[0])) <= max(3, 0.05 * it[0])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fcg_mixed_plain_box(box8, use_graph):
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    u, stats, st = M.solve(cuda(f), solver="fcg_mixed", tol=1e-8, use_graph=use_graph)
+    assert st == 0
+    assert stats[0]["relres"] <= 1e-8
+    ud = oracle.direct_solve(K, f)
+    assert rel_l2(u.cpu().numpy(), ud) <= 1e-6
+    _, outer, inner, _ = oracle.fcg_mixed(K, f, tol=1e-8)
+    assert abs(stats[0]["outer"] - int(outer[0])) <= max(2, 0.25 * outer[0])
+    assert stats[0]["inner"] <= 30 * stats[0]["outer"]
+
+
+@pytest.mark.gpu
+def test_fcg_zero_inner_steps_tracks_pcg(box8):
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    _, sp, _ = M.solve(cuda(f), solver="pcg64", tol=1e-8)
+    _, sf, st = M.solve(cuda(f), solver="fcg_mixed", tol=1e-8, n_inner=0)
+    assert st == 0 and sf[0]["inner"] == 0
+    assert abs(sf[0]["outer"] - sp[0]["outer"]) <= max(3, 0.05 * sp[0]["outer"])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solver", ["pcg64", "fcg_mixed"])
+def test_batched_uneven_cases_with_zero_rhs(box8, solver):
+    """Four cases of different difficulty plus an all-zero case: per-case masking."""
+    m, K, M = box8
+    lx, ly, lz = m.lattice_shape()
+    cases = [mg.plain_box_rhs(m)[:, 0],
+             mg.double_couple(m, (lx // 2 - 5, ly // 2 + 3, lz - 3), 1e12),
+             np.zeros((m.n_nodes, 3)),
+             mg.random_vectors(m.n_nodes, 1, seed=3)[:, 0] * 1e9 * m.free]
+    f = np.stack(cases, axis=1)
+    u, stats, st = M.solve(cuda(f), solver=solver, tol=1e-8)
+    assert st == 0, stats
+    u = u.cpu().numpy()
+    ud = oracle.direct_solve(K, f)
+    for r in (0, 1, 3):
+        assert stats[r]["relres"] <= 1e-8
+        assert rel_l2(u[:, r], ud[:, r]) <= 1e-6
+    assert np.all(u[:, 2] == 0.0) and stats[2]["outer"] == 0
+    its = [stats[r]["outer"] for r in (0, 1, 3)]
+    assert len(set(its)) > 1          # the cases really stopped at different iterations
+
+
+@pytest.mark.gpu
+def test_iteration_cap_reports_noconv(box8):
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    u, stats, st = M.solve(cuda(f), solver="fcg_mixed", max_outer=2, raise_on_fail=False)
+    from paper_1710_08679_gb300 import fe
+    assert st == fe.FE_ENOCONV
+    assert stats[0]["status"] == fe.FE_ENOCONV and stats[0]["outer"] == 2
+    assert stats[0]["relres"] > 1e-8 and np.isfinite(stats[0]["relres"])
+
+
+@pytest.mark.gpu
+def test_warm_start_from_solution(box8):
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    u, s1, _ = M.solve(cuda(f), solver="fcg_mixed", tol=1e-9)
+    u2, s2, st = M.solve(cuda(f), u0=u, solver="fcg_mixed", tol=1e-8)
+    assert st == 0 and s2[0]["outer"] == 0 and s2[0]["relres"] <= 1e-8
+
+
+@pytest.mark.gpu
+def test_slip_sources_on_ragged_crust():
+    """Split-node unit-slip sources: f = -sum_{e in E+} K_e s_e computed by the GPU
+    (fe_ebe_apply on the hanging-wall sub-mesh) and by the oracle (assembled sub-mesh
+    matrix), then a batched mixed solve against the oracle's direct solve."""
+    m, iface = mg.crust_block(shape=(12, 6, 6), h=1000.0, jitter=0.15, seed=1)
+    cases = mg.patch_grid_cases(m, iface, n_along=2, spacing=2000.0, size=2000.0)
+    cases = [c for c in cases if len(c.elems)][:3]
+    assert len(cases) >= 2
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    from paper_1710_08679_gb300 import fe
+    f_gpu, f_ref = [], []
+    for c in cases:
+        sub = mg.Mesh(coords=m.coords, conn=m.conn[c.elems], young=m.young[c.elems], poisson=m.poisson[c.elems],
+                      free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
+        Ms = fe.Mesh.from_mesh(sub)
+        f_gpu.append(-(Ms.ebe(cuda(c.slip[:, None, :])).cpu().numpy()[:, 0]) * m.free)
+        Ks = oracle.assemble(sub, apply_bc=False)
+        f_ref.append(-oracle.spmv(Ks, c.slip[:, None, :])[:, 0] * m.free)
+    f_gpu = np.stack(f_gpu, axis=1)
+    f_ref = np.stack(f_ref, axis=1)
+    assert rel_l2(f_gpu, f_ref) <= 1e-12
+    u, stats, st = M.solve(cuda(f_gpu), solver="fcg_mixed", tol=1e-8)
+    assert st == 0
+    ud = oracle.direct_solve(K, f_ref)
+    for r in range(len(cases)):
+        assert stats[r]["relres"] <= 1e-8
+        assert rel_l2(u.cpu().numpy()[:, r], ud[:, r]) <= 1e-5
+
+
+@pytest.mark.gpu
+def test_adjoint_grad_matches_oracle(box8):
+    m, K, M = box8
+    u = mg.random_vectors(m.n_nodes, 3, seed=21)
+    lam = mg.random_vectors(m.n_nodes, 3, seed=22)
+    g = M.adjoint_grad(cuda(u), cuda(lam)).cpu().numpy()
+    ref = oracle.adjoint_grad(m, u, lam)
+    assert rel_l2(g, ref) <= 1e-12
+
+
+@pytest.mark.gpu
+def test_set_log_young_changes_operator(box8):
+    m, K, _ = box8
+    M = gpu_mesh(m)
+    rng = np.random.default_rng(5)
+    le = np.log(m.young) + 0.1 * rng.standard_normal(m.n_elem)
+    M.set_log_young(cuda(le))
+    x = mg.random_vectors(m.n_nodes, 2, seed=8)
+    y = M.ebe(cuda(x)).cpu().numpy()
+    K2 = oracle.assemble(m, young=np.exp(le))
+    assert rel_l2(y, oracle.spmv(K2, x)) <= 1e-12
