@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the R / precision sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
+    ap.add_argument("--profile", action="store_true",
+                    help="EBE timing only, kernel fixed by --variant/--tile (no tuning, e2e, sweep, solve, CPU)")
+    ap.add_argument("--variant", default="direct", choices=["direct", "tiled"], help="kernel for --profile")
+    ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
     return ap.parse_args()
 
 
@@ -255,6 +260,15 @@ def run_ours(args):
     N, E = m.n_nodes, m.n_elem
     M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
     R = R_MAIN
+    if args.profile:
+        M.set_variant(R, args.dtype, 1 if args.variant == "tiled" else 0, args.tile)
+        tt = torch.float32 if args.dtype == "f32" else torch.float64
+        x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R)).to("cuda", tt)
+        y = torch.empty_like(x)
+        ms, per = time_ebe(M, x, y, args.steps, args.warmup, torch)
+        print(json.dumps({"profile": True, "variant": args.variant, "tile": args.tile, "dtype": args.dtype, "R": R,
+                          "ms_per_product": ms / args.steps, "per_step_ms": per}), flush=True)
+        return
     v32, us32 = M.tune(R, "f32")
     x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R + rank).astype(np.float32)).cuda()
     y = torch.empty_like(x)
