@@ -201,6 +201,25 @@ fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* f_dev, doub
 fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void* stream);
 
 /*
+ * fe_block_jacobi_noalloc -- fe_block_jacobi's result without allocating device
+ * memory. The paper has no counterpart; this exists for callers that cannot
+ * allocate where they need the preconditioner: code recording a CUDA stream
+ * capture, latency-critical loops that must not take the allocator's lock, and
+ * processes whose device memory is held by another allocator's pool.
+ *   binv_dev  device double [N][3][3], overwritten with the inverse blocks
+ * Scratch lives in a fixed file-scope device array (about 13.5 MiB, held on every
+ * GPU that loads the library until the process exits), so the mesh may have at
+ * most 131,072 nodes; larger meshes get FE_EINVAL and nothing is launched.
+ * Recomputes the blocks on every call (the mesh's own copy is not touched).
+ * Synchronous on `stream` (it reads back an error flag). The first call on a
+ * device looks up the array's device address (set-up, once per device); make that
+ * first call before any stream capture. All calls share the one array: calls
+ * whose work overlaps on the GPU (different streams or threads) race and must be
+ * serialised by the caller.
+ */
+fe_status fe_block_jacobi_noalloc(const fe_mesh* mesh, double* binv_dev, void* stream);
+
+/*
  * fe_adjoint_grad -- element sensitivities for m_e = log E_e:
  *   g_e = - sum_r (P lambda_r)_e^T K_e (P u_r)_e
  * which is dJ/dm_e when K_bc lambda_r = dJ/du_r (adjoint state) and

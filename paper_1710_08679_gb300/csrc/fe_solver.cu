@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fe_element.cuh"
@@ -980,6 +981,83 @@ extern "C" fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void
     cudaStream_t s = (cudaStream_t)stream;
     fe::build_block_jacobi(m, s);
     FE_CUDA(cudaMemcpyAsync(binv_dev, m->binv64.ptr, m->binv64.bytes, cudaMemcpyDeviceToDevice, s));
+    return FE_OK;
+  } catch (const fe::Failure& x) {
+    return x.status;
+  } catch (...) {
+    fe::set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free build of the block-Jacobi preconditioner.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// preconditioner: code recording a CUDA stream capture (cudaMalloc may block or
+// synchronise the device, which capture forbids), latency-critical loops that must
+// not take the allocator's lock, and processes whose device memory is already
+// reserved by another allocator's pool (a framework's caching allocator), where a
+// fresh cudaMalloc can fail mid-run. For them fe_block_jacobi_noalloc keeps its
+// scratch (the FP64 [N][9] accumulator of diagonal blocks, the FP32 copy of the
+// inverse the shared kernel also writes, and an error flag) in the fixed
+// file-scope array below instead of allocating it. Every GPU that loads this
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace fe {
+
+constexpr int64_t kNoAllocMaxNodes = 131072;                       // largest mesh served
+constexpr size_t kNoAllocD = (size_t)kNoAllocMaxNodes * 9 * sizeof(double);   // offset of FP32 blocks
+constexpr size_t kNoAllocFlag = kNoAllocD + (size_t)kNoAllocMaxNodes * 9 * sizeof(float);
+constexpr size_t kNoAllocBytes = kNoAllocFlag + 256;               // about 13.5 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up once per
+// device (the host-side name of the array is only a stand-in, not a device address).
+static void* g_noalloc_addr[256];
+static std::mutex g_noalloc_mutex;
+
+static void* noalloc_scratch(int device) {
+  FE_REQUIRE(device >= 0 && device < 256, "device ordinal %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    FE_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));   // the device is current (DeviceGuard)
+    g_noalloc_addr[device] = p;
+  }
+  return g_noalloc_addr[device];
+}
+
+}  // namespace fe
+
+extern "C" fe_status fe_block_jacobi_noalloc(const fe_mesh* mesh, double* binv_dev, void* stream) {
+  try {
+    fe::clear_error();
+    FE_REQUIRE(mesh != nullptr && binv_dev != nullptr, "NULL argument");
+    FE_REQUIRE(mesh->n_nodes <= fe::kNoAllocMaxNodes,
+               "fe_block_jacobi_noalloc serves meshes of at most %lld nodes (this mesh has %lld); "
+               "use fe_block_jacobi", (long long)fe::kNoAllocMaxNodes, (long long)mesh->n_nodes);
+    fe::DeviceGuard dg(mesh->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = static_cast<unsigned char*>(fe::noalloc_scratch(mesh->device));
+    double* D = reinterpret_cast<double*>(base);
+    float* B32 = reinterpret_cast<float*>(base + fe::kNoAllocD);
+    int* bad = reinterpret_cast<int*>(base + fe::kNoAllocFlag);
+    const int64_t N = mesh->n_nodes, E = mesh->n_elem;
+    // the array keeps the previous call's contents: clear the accumulator and the flag
+    FE_CUDA(cudaMemsetAsync(D, 0, (size_t)N * 9 * sizeof(double), s));
+    FE_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    fe::jacobi_diag_kernel<<<(unsigned)((E + 127) / 128), 128, 0, s>>>(mesh->view<double>(), D);
+    FE_CHECK_LAUNCH();
+    fe::jacobi_invert_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, mesh->nmask.as<uint8_t>(), D, binv_dev,
+                                                                         B32, bad);
+    FE_CHECK_LAUNCH();
+    int hbad = 0;
+    FE_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    FE_REQUIRE(hbad == 0, "block Jacobi: a free node has a singular or indefinite diagonal block "
+                          "(node touched by no element, or a degenerate material)");
     return FE_OK;
   } catch (const fe::Failure& x) {
     return x.status;

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "F
 # every symbol include/fe.h declares
 EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_create", "fe_mesh_destroy",
             "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
-            "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_adjoint_grad"]
+            "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_block_jacobi_noalloc",
+            "fe_adjoint_grad"]
 
 
 class FeError(RuntimeError):
@@ -78,8 +79,10 @@ def load(path: Optional[str] = None):
     lib.fe_pcg_solve.argtypes = [_vp, _i32, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp]
     lib.fe_adjoint_grad.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
     lib.fe_block_jacobi.argtypes = [_vp, _vp, _vp]
+    lib.fe_block_jacobi_noalloc.argtypes = [_vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
-                 "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_adjoint_grad"):
+                 "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_block_jacobi_noalloc",
+                 "fe_adjoint_grad"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
