@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
     ap.add_argument("--profile", action="store_true",
                     help="EBE timing only, kernel fixed by --variant/--tile (no tuning, e2e, sweep, solve, CPU)")
-    ap.add_argument("--variant", default="direct", choices=["direct", "tiled"], help="kernel for --profile")
+    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather"], help="kernel for --profile")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
     return ap.parse_args()
@@ -261,7 +261,7 @@ def run_ours(args):
     M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
     R = R_MAIN
     if args.profile:
-        M.set_variant(R, args.dtype, 1 if args.variant == "tiled" else 0, args.tile)
+        M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2}[args.variant], args.tile)
         tt = torch.float32 if args.dtype == "f32" else torch.float64
         x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R)).to("cuda", tt)
         y = torch.empty_like(x)
@@ -270,6 +270,8 @@ def run_ours(args):
                           "ms_per_product": ms / args.steps, "per_step_ms": per}), flush=True)
         return
     v32, us32 = M.tune(R, "f32")
+    kind_name = {0: "direct", 1: "tiled", 2: "gather"}[v32 // 65536]
+    kernel_desc = kind_name + ("" if v32 // 65536 == 0 else " %d elements/tile" % (v32 % 65536))
     x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R + rank).astype(np.float32)).cuda()
     y = torch.empty_like(x)
 
@@ -324,13 +326,13 @@ def run_ours(args):
     if os.path.exists(tp):
         try:
             tj = json.load(open(tp))
-            if tj.get("variant") == int(v32) and tj.get("shape") == list(shape) and tj.get("R") == R:
+            if tj.get("variant") == kernel_desc and tj.get("shape") == list(shape) and tj.get("R") == R:
                 traffic = tj.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "fe_ebe_apply (y init + %s EBE kernel)" % ("tiled" if v32 else "direct"),
+                "kernel": "fe_ebe_apply (zero pass + %s EBE kernel)" % kernel_desc,
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                         "peak_source": peak_src, "algorithmic_bytes": bytes_alg}}
@@ -339,7 +341,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "crust_%dx%dx%d_tet10_R%d_fp32_ebe" % (shape + (R,)), "mesh_elements": E,
-                      "mesh_dof": 3 * N, "R": R, "kernel_variant": int(v32),
+                      "mesh_dof": 3 * N, "R": R, "kernel_variant": kernel_desc,
                       "l2": "inputs larger than L2 (x and y %d MB each), no flush" % (x.numel() * 4 // 2 ** 20),
                       "parallelism": "case-sharded replicas x%d" % world},
            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "clocks": clocks}
@@ -354,8 +356,10 @@ def run_ours(args):
                 yy = torch.empty_like(xx)
                 ms, _ = time_ebe(M, xx, yy, 5 if dt == "f64" else 10, 2, torch)
                 n = 5 if dt == "f64" else 10
+                kv, kt = M.get_variant(RR, dt)
                 sweep[f"{dt}_R{RR}"] = {"GDOF_cases_per_s": 3.0 * N * RR / (ms / n * 1e-3) / 1e9,
-                                        "ms": ms / n, "variant": M.get_variant(RR, dt)[1]}
+                                        "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather"}[kv],
+                                        "tile": kt}
                 del xx, yy
         out["ebe_sweep"] = sweep
 

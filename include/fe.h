@@ -140,15 +140,20 @@ fe_status fe_mesh_set_log_young(fe_mesh* mesh, const double* logE_dev, void* str
 fe_status fe_ebe_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x_dev, void* y_dev,
                        void* stream);
 
-/* EBE kernel variants (both compute fe_ebe_apply's result):
+/* EBE kernel variants (all compute fe_ebe_apply's result):
  *   FE_EBE_DIRECT  one thread per (element, case), inputs gathered from global
  *                  memory, results added with global atomics (the paper's GPU
  *                  port keeps atomics rather than element colouring, Sec. 3.2.2);
  *   FE_EBE_TILED   consecutive elements (in the library's locality order) form a
  *                  tile; the tile's node values are staged in shared memory, the
- *                  element products accumulate there, and each tile node gets one
- *                  global atomic add per value. */
-typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1 } fe_ebe_variant;
+ *                  element products accumulate there with shared-memory atomics,
+ *                  and each tile node gets one global atomic add per value;
+ *   FE_EBE_GATHER  tiles as above, but without atomics inside the tile: every
+ *                  element-case product is written to its own shared-memory slot,
+ *                  then each tile node sums the slots of its incident elements
+ *                  and issues one 16-byte global atomic add per 16 bytes of
+ *                  values (R in {1, 2, 3, 4, 8, 16, 32}). */
+typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1, FE_EBE_GATHER = 2 } fe_ebe_variant;
 
 /*
  * fe_ebe_set_variant -- choose the kernel fe_ebe_apply (and the solvers) use for
@@ -164,11 +169,11 @@ fe_status fe_ebe_get_variant(const fe_mesh* mesh, int32_t R, fe_dtype dtype, int
                              int32_t* tile_elems);
 
 /*
- * fe_ebe_tune -- autotuner: times the direct kernel and the tiled kernel at
- * 24/48/96/192/384 elements per tile (where it fits) for (R, dtype) on this mesh,
- * using library-owned scratch vectors, and selects the fastest. Synchronous.
- * *variant receives 0 for direct or the chosen tile size; *us its time per
- * product in microseconds.
+ * fe_ebe_tune -- autotuner: times the direct kernel and the tiled and gather
+ * kernels over a range of tile sizes (where they fit) for (R, dtype) on this
+ * mesh, using library-owned scratch vectors, and selects the fastest.
+ * Synchronous. *variant receives kind * 65536 + elements per tile of the choice
+ * (0 = direct); *us its time per product in microseconds.
  */
 fe_status fe_ebe_tune(fe_mesh* mesh, int32_t R, fe_dtype dtype, void* stream, int32_t* variant, int32_t* us);
 

@@ -128,6 +128,9 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
   std::vector<int32_t> ptr((size_t)nt + 1, 0);
   std::vector<int32_t> ids;
   std::vector<uint16_t> lconn((size_t)E * 10);
+  std::vector<uint16_t> inc((size_t)E * 10);
+  std::vector<uint16_t> inc_start;
+  inc_start.reserve((size_t)E * 3);
   ids.reserve((size_t)E * 3);
   std::vector<int32_t> buf;
   std::vector<uint8_t> own;
@@ -139,7 +142,7 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
     buf.assign(m->conn_host.begin() + 10 * e0, m->conn_host.begin() + 10 * e1);
     std::sort(buf.begin(), buf.end());
     buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-    FE_REQUIRE(buf.size() <= 65535, "tile too large");
+    FE_REQUIRE(buf.size() <= 65535 && (e1 - e0) * 10 <= 65535, "tile too large");
     max_nodes = std::max(max_nodes, (int)buf.size());
     for (int64_t e = e0; e < e1; ++e)
       for (int a = 0; a < 10; ++a) {
@@ -152,17 +155,62 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
       own.push_back(seen[(size_t)g] ? 0 : 1);
       seen[(size_t)g] = 1;
     }
+    // element-node slots of the tile grouped by local node (counting sort)
+    const int nn = (int)buf.size();
+    std::vector<int> cnt((size_t)nn + 1, 0);
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = 0; a < 10; ++a) cnt[(size_t)lconn[(size_t)(10 * e + a)] + 1]++;
+    for (int i = 0; i < nn; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+    for (int i = 0; i < nn; ++i) inc_start.push_back((uint16_t)cnt[(size_t)i]);
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = 0; a < 10; ++a) {
+        const int ln = lconn[(size_t)(10 * e + a)];
+        inc[(size_t)(10 * e0 + cnt[(size_t)ln]++)] = (uint16_t)((e - e0) * 10 + a);
+      }
     ptr[(size_t)ti + 1] = (int32_t)ids.size();
   }
   t.node_ptr.alloc(ptr.size() * sizeof(int32_t));
   t.node_ids.alloc(ids.size() * sizeof(int32_t));
   t.lconn.alloc(lconn.size() * sizeof(uint16_t));
   t.node_own.alloc(own.size());
+  t.inc.alloc(inc.size() * sizeof(uint16_t));
+  t.inc_start.alloc(inc_start.size() * sizeof(uint16_t));
+  FE_CUDA(cudaMemcpyAsync(t.inc.ptr, inc.data(), inc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(t.inc_start.ptr, inc_start.data(), inc_start.size() * sizeof(uint16_t),
+                          cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(t.node_own.ptr, own.data(), own.size(), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(t.node_ptr.ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(t.node_ids.ptr, ids.data(), ids.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(t.lconn.ptr, lconn.data(), lconn.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaStreamSynchronize(s));
+  // packets: one contiguous block per tile
+  {
+    const PacketLayout L(max_nodes, tile_elems);
+    std::vector<unsigned char> pk((size_t)nt * L.bytes, 0);
+    for (int64_t ti = 0; ti < nt; ++ti) {
+      unsigned char* b = pk.data() + (size_t)ti * L.bytes;
+      const int64_t e0 = ti * tile_elems, e1 = std::min(E, e0 + tile_elems);
+      const int p0 = ptr[(size_t)ti], nn = ptr[(size_t)ti + 1] - p0, ne = (int)(e1 - e0);
+      int32_t hdr[4] = {nn, ne, 0, 0};
+      std::memcpy(b, hdr, 16);
+      std::memcpy(b + L.ids, &ids[(size_t)p0], (size_t)nn * 4);
+      for (int i = 0; i < nn; ++i) {
+        const int32_t g = ids[(size_t)p0 + i];
+        const uint8_t mk = (uint8_t)(m->nmask_host[(size_t)g]);
+        b[L.mask + i] = mk;
+        b[L.own + i] = own[(size_t)p0 + i];
+      }
+      std::memcpy(b + L.inc_start, &inc_start[(size_t)p0], (size_t)nn * 2);
+      const uint16_t endv = (uint16_t)(ne * 10);
+      std::memcpy(b + L.inc_start + 2 * nn, &endv, 2);
+      std::memcpy(b + L.lconn, &lconn[(size_t)e0 * 10], (size_t)ne * 20);
+      std::memcpy(b + L.inc, &inc[(size_t)e0 * 10], (size_t)ne * 20);
+    }
+    t.packets.alloc(pk.size());
+    FE_CUDA(cudaMemcpyAsync(t.packets.ptr, pk.data(), pk.size(), cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    t.packet_bytes = L.bytes;
+  }
   t.tile_elems = tile_elems;
   t.max_nodes = max_nodes;
   t.n_tiles = nt;
@@ -317,6 +365,7 @@ fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, 
     FE_CUDA(cudaMemcpyAsync(m->xyz64.ptr, coords, m->xyz64.bytes, cudaMemcpyHostToDevice, s));
     FE_CUDA(cudaMemcpyAsync(m->xyz32.ptr, xyz32.data(), m->xyz32.bytes, cudaMemcpyHostToDevice, s));
     FE_CUDA(cudaMemcpyAsync(m->nmask.ptr, nm.data(), m->nmask.bytes, cudaMemcpyHostToDevice, s));
+    m->nmask_host = nm;
     FE_CUDA(cudaMemcpyAsync(m->perm.ptr, m->perm_host.data(), m->perm.bytes, cudaMemcpyHostToDevice, s));
     upload_materials(m, s);
     *out = m;
@@ -369,16 +418,20 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
   return guarded([&] {
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
-    FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED, "unknown variant %d", variant);
+    FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER,
+               "unknown variant %d", variant);
     DeviceGuard dg(m->device);
-    if (variant == FE_EBE_TILED) {
-      get_tiling(m, tile_elems, (cudaStream_t)stream);
-      FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32),
-                 "tile of %d elements does not fit in shared memory for R = %d", tile_elems, R);
-      ebe_set_variant(m, R, dtype == FE_F32, tile_elems);
-    } else {
+    if (variant == FE_EBE_DIRECT) {
       ebe_set_variant(m, R, dtype == FE_F32, 0);
+      return;
     }
+    FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),
+               "the gather kernel is compiled for R in {1, 2, 3, 4, 8, 16, 32}, not %d", R);
+    get_tiling(m, tile_elems, (cudaStream_t)stream);
+    if (variant == FE_EBE_GATHER) ensure_geometry_buffer(m, dtype == FE_F32);
+    FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32, variant),
+               "tile of %d elements does not fit in shared memory for R = %d", tile_elems, R);
+    ebe_set_variant(m, R, dtype == FE_F32, variant * 65536 + tile_elems);
   });
 }
 
@@ -387,8 +440,8 @@ fe_status fe_ebe_get_variant(const fe_mesh* m, int32_t R, fe_dtype dtype, int32_
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     const int v = ebe_get_variant(m, R, dtype == FE_F32);
-    if (variant) *variant = v > 0 ? FE_EBE_TILED : FE_EBE_DIRECT;
-    if (tile_elems) *tile_elems = v > 0 ? v : 0;
+    if (variant) *variant = v / 65536;
+    if (tile_elems) *tile_elems = v % 65536;
   });
 }
 

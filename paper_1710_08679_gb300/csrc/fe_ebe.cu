@@ -219,6 +219,474 @@ __global__ void __launch_bounds__(kThreads) ebe_tiled_kernel(MeshView<T> M, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// gather kernel: CTA = tile of elements, no atomics inside the tile.
+//   phase 1  node ids, masks, slot lists, element geometry -> shared; the tile's
+//            node inputs -> xs [nn][3R] (16-byte loads)
+//   phase 2  thread = (element, case): u from xs, y_e = K_e u_e, the 30 results
+//            written to the element's own slot ob[le][a][3R] (plain stores;
+//            the element stride S = 30R + (3R mod 32) keeps the lanes of
+//            neighbouring elements on different banks)
+//   phase 3  thread = (tile node, 16 bytes of its 3R values): sum of the slots
+//            of the node's incident elements (16-byte loads), one 16-byte global
+//            atomic add (free DOFs) or the owner's store of x (constrained DOFs)
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+struct GatherCfg {
+  static constexpr int VR = 3 * R;                      // values per node
+  static constexpr int V = 16 / (int)sizeof(T);         // values per 16-byte vector
+  static constexpr bool VEC = (VR % V) == 0;
+  static constexpr int S = 30 * R + ((3 * R) % 32);     // element slot stride
+};
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+__device__ __forceinline__ float vget(const float4& v, int t) {
+  return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double vget(const double2& v, int t) { return t == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4& v, int t, float x) {
+  if (t == 0) v.x = x; else if (t == 1) v.y = x; else if (t == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void vset(double2& v, int t, double x) {
+  if (t == 0) v.x = x; else v.y = x;
+}
+__device__ __forceinline__ void vadd(float4& a, const float4& b) {
+  a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+}
+__device__ __forceinline__ void vadd(double2& a, const double2& b) {
+  a.x += b.x; a.y += b.y;
+}
+__device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vzero(double2& a) { a = make_double2(0.0, 0.0); }
+__device__ __forceinline__ void vred(float4* p, const float4& v) { atomicAdd(p, v); }
+__device__ __forceinline__ void vred(double2* p, const double2& v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename T, int R>
+__host__ __device__ size_t gather_smem_bytes(int nn, int te) {
+  using C = GatherCfg<T, R>;
+  return align16((size_t)nn * C::VR * sizeof(T)) + align16((size_t)te * C::S * sizeof(T)) +
+         align16((size_t)te * kGeo * sizeof(T)) + align16((size_t)nn * sizeof(int)) +
+         align16((size_t)te * 10 * sizeof(uint16_t)) * 2 + align16((size_t)(nn + 1) * sizeof(uint16_t)) +
+         align16((size_t)nn) * 2;
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads) ebe_gather_kernel(MeshView<T> M, int tile_elems,
+                                                              const int32_t* __restrict__ node_ptr,
+                                                              const int32_t* __restrict__ node_ids,
+                                                              const uint8_t* __restrict__ node_own,
+                                                              const uint16_t* __restrict__ lconn,
+                                                              const uint16_t* __restrict__ inc,
+                                                              const uint16_t* __restrict__ inc_start,
+                                                              const T* __restrict__ x, T* __restrict__ y,
+                                                              const int* __restrict__ skip) {
+  using C = GatherCfg<T, R>;
+  using VT = typename Vec16<T>::type;
+  constexpr int VR = C::VR, V = C::V, S = C::S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (skip && *skip) return;
+  const int64_t tile = blockIdx.x;
+  const int nb = __ldg(node_ptr + tile);
+  const int nn = __ldg(node_ptr + tile + 1) - nb;
+  const int64_t e0 = tile * (int64_t)tile_elems;
+  const int64_t rem = M.n_elem - e0;
+  const int ne = rem < (int64_t)tile_elems ? (int)rem : tile_elems;
+
+  unsigned char* sp = smem_raw;
+  T* xs = reinterpret_cast<T*>(sp);
+  sp += align16((size_t)nn * VR * sizeof(T));
+  T* ob = reinterpret_cast<T*>(sp);
+  sp += align16((size_t)tile_elems * S * sizeof(T));
+  T* geo = reinterpret_cast<T*>(sp);
+  sp += align16((size_t)tile_elems * kGeo * sizeof(T));
+  int* ids = reinterpret_cast<int*>(sp);
+  sp += align16((size_t)nn * sizeof(int));
+  uint16_t* lc = reinterpret_cast<uint16_t*>(sp);
+  sp += align16((size_t)tile_elems * 10 * sizeof(uint16_t));
+  uint16_t* ic = reinterpret_cast<uint16_t*>(sp);
+  sp += align16((size_t)tile_elems * 10 * sizeof(uint16_t));
+  uint16_t* is = reinterpret_cast<uint16_t*>(sp);
+  sp += align16((size_t)(nn + 1) * sizeof(uint16_t));
+  unsigned char* mks = sp;
+  sp += align16((size_t)nn);
+  unsigned char* own = sp;
+
+  // ---- phase 1
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+    const int g = __ldg(node_ids + nb + i);
+    ids[i] = g;
+    mks[i] = __ldg(M.nmask + g);
+    own[i] = __ldg(node_own + nb + i);
+    is[i] = __ldg(inc_start + nb + i);
+  }
+  if (threadIdx.x == 0) is[nn] = (uint16_t)(ne * 10);
+  for (int i = threadIdx.x; i < ne * 10; i += blockDim.x) {
+    lc[i] = __ldg(lconn + 10 * e0 + i);
+    ic[i] = __ldg(inc + 10 * e0 + i);
+  }
+  for (int le = threadIdx.x; le < ne; le += blockDim.x) {
+    int nd[10];
+    load_conn<T>(M.conn, e0 + le, nd);
+    ElemGeo<T> G;
+    load_geometry(M, e0 + le, nd, G);
+    T* gp = geo + le * kGeo;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gp[3 * k + i] = G.g[k][i];
+    gp[12] = G.lam;
+    gp[13] = G.mu;
+    gp[14] = G.c;
+  }
+  __syncthreads();
+  if constexpr (C::VEC) {
+    constexpr int CPN = VR / V;   // 16-byte chunks per node
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      VT v = __ldg(reinterpret_cast<const VT*>(x + (int64_t)ids[ln] * VR) + q);
+      const int mk = mks[ln];
+      if (mk != 7) {
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+          if (!((mk >> ((q * V + t) % 3)) & 1)) vset(v, t, T(0));
+      }
+      reinterpret_cast<VT*>(xs + ln * VR)[q] = v;
+    }
+  } else {
+    for (int k = threadIdx.x; k < nn * VR; k += blockDim.x) {
+      const int ln = k / VR;
+      const int w = k - ln * VR;
+      const T v = __ldg(x + (int64_t)ids[ln] * VR + w);
+      xs[k] = ((mks[ln] >> (w % 3)) & 1) ? v : T(0);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2
+  for (int it = threadIdx.x; it < ne * R; it += blockDim.x) {
+    const int le = it / R;
+    const int r = it - le * R;
+    ElemGeo<T> G;
+    const T* gp = geo + le * kGeo;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) G.g[k][i] = gp[3 * k + i];
+    G.lam = gp[12];
+    G.mu = gp[13];
+    G.c = gp[14];
+    T u[10][3];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      const T* xa = xs + lc[10 * le + a] * VR + 3 * r;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[a][c] = xa[c];
+    }
+    T yl[10][3];
+    elem_apply(G, u, yl);
+    T* o = ob + le * S + 3 * r;
+#pragma unroll
+    for (int a = 0; a < 10; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[a * VR + c] = yl[a][c];
+  }
+  __syncthreads();
+
+  // ---- phase 3
+  if constexpr (C::VEC) {
+    constexpr int CPN = VR / V;
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      VT acc;
+      vzero(acc);
+      const int j1 = is[ln + 1];
+      for (int j = is[ln]; j < j1; ++j) {
+        const int code = ic[j];
+        const int le = code / 10;
+        const int a = code - 10 * le;
+        vadd(acc, reinterpret_cast<const VT*>(ob + le * S + a * VR)[q]);
+      }
+      const int64_t gi = (int64_t)ids[ln] * VR + q * V;
+      const int mk = mks[ln];
+      if (mk == 7) {
+        vred(reinterpret_cast<VT*>(y + gi), acc);
+      } else {
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          if ((mk >> ((q * V + t) % 3)) & 1)
+            atomicAdd(y + gi + t, vget(acc, t));
+          else if (own[ln])
+            y[gi + t] = __ldg(x + gi + t);
+        }
+      }
+    }
+  } else {
+    for (int k = threadIdx.x; k < nn * VR; k += blockDim.x) {
+      const int ln = k / VR;
+      const int w = k - ln * VR;
+      T acc = T(0);
+      const int j1 = is[ln + 1];
+      for (int j = is[ln]; j < j1; ++j) {
+        const int code = ic[j];
+        const int le = code / 10;
+        const int a = code - 10 * le;
+        acc += ob[le * S + a * VR + w];
+      }
+      const int64_t gi = (int64_t)ids[ln] * VR + w;
+      if ((mks[ln] >> (w % 3)) & 1)
+        atomicAdd(y + gi, acc);
+      else if (own[ln])
+        y[gi] = __ldg(x + gi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pipelined gather kernel (persistent CTAs).
+// A prep pass computes every element's geometry once per product (from the node
+// coordinates and (E, nu), as the product requires) into geo[E][16] and zeroes y.
+// Each CTA then walks its tiles t = blockIdx.x, + gridDim.x, ... with cp.async
+// prefetch: while tile i is computed, the inputs of tile i+1 (gathered by node
+// id) and the packet of tile i+2 are in flight. Phases 2 and 3 are those of the
+// gather kernel. cp.async groups are waited with cp.async.wait_group (hardware
+// wait, no spinning).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prep_kernel(MeshView<T> M, T* __restrict__ geo, int64_t nv,
+                                                        T* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using VT = typename Vec16<T>::type;
+  constexpr int V = 16 / (int)sizeof(T);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t e = gid; e < M.n_elem; e += stride) {
+    int nd[10];
+    load_conn<T>(M.conn, e, nd);
+    ElemGeo<T> G;
+    load_geometry(M, e, nd, G);
+    T v[kGeo];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[3 * k + i] = G.g[k][i];
+    v[12] = G.lam;
+    v[13] = G.mu;
+    v[14] = G.c;
+    v[15] = T(0);
+    VT* dst = reinterpret_cast<VT*>(geo + e * kGeo);
+#pragma unroll
+    for (int q = 0; q < kGeo / V; ++q) {
+      VT w;
+#pragma unroll
+      for (int t = 0; t < V; ++t) vset(w, t, v[q * V + t]);
+      dst[q] = w;
+    }
+  }
+  const int64_t n16 = nv * (int64_t)sizeof(T) / 16;
+  VT z;
+  vzero(z);
+  for (int64_t i = gid; i < n16; i += stride) reinterpret_cast<VT*>(y)[i] = z;
+  for (int64_t i = n16 * V + gid; i < nv; i += stride) y[i] = T(0);
+}
+
+template <typename T, int R>
+__host__ __device__ size_t pipe_smem_bytes(int nnmax, int te, int pk) {
+  using C = GatherCfg<T, R>;
+  return (size_t)3 * pk + (size_t)3 * te * kGeo * sizeof(T) + (size_t)2 * nnmax * C::VR * sizeof(T) +
+         (size_t)te * C::S * sizeof(T) + (size_t)((te * 10 + 3) & ~3) * sizeof(int) + (size_t)te * 12 * sizeof(int);
+}
+
+// FP32: up to 1024 threads per block (one thread per element-case item of a tile,
+// at most 64 registers); FP64 keeps 256-thread blocks.
+template <typename T>
+struct PipeThreads {
+  static constexpr int value = sizeof(T) == 4 ? 1024 : kThreads;
+};
+
+template <typename T, int R>
+__global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t n_tiles, int64_t n_elem, int te, int nnmax,
+                                                            const unsigned char* __restrict__ packets, int pk,
+                                                            const T* __restrict__ geo, const T* __restrict__ x,
+                                                            T* __restrict__ y, const int* __restrict__ skip) {
+  using C = GatherCfg<T, R>;
+  using VT = typename Vec16<T>::type;
+  constexpr int VR = C::VR, V = C::V, S = C::S, CPN = VR / V;
+  static_assert(C::VEC, "pipelined kernel needs 16-byte node rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (skip && *skip) return;
+  const PacketLayout L(nnmax, te);
+  unsigned char* meta = smem_raw;                                   // [3][pk]
+  T* geo_s = reinterpret_cast<T*>(meta + 3 * (size_t)pk);           // [3][te][16]
+  T* xs = geo_s + 3 * (size_t)te * kGeo;                            // [2][nnmax][VR]
+  T* ob = xs + 2 * (size_t)nnmax * VR;                              // [te][S]
+  int* io = reinterpret_cast<int*>(ob + (size_t)te * S);            // [te*10] slot offsets in ob, by node
+  int* no = io + ((te * 10 + 3) & ~3);                             // [te][12] node row offsets in xs (16-byte aligned)
+  const int64_t G = gridDim.x;
+  int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+
+  auto issue_meta = [&](int64_t tile, int stage) {
+    const unsigned char* src = packets + tile * (int64_t)pk;
+    unsigned char* dst = meta + (size_t)stage * pk;
+    for (int k = threadIdx.x; k < pk / 16; k += blockDim.x) cp_async16(dst + 16 * k, src + 16 * k);
+    const int64_t rem = n_elem - tile * (int64_t)te;
+    const int ne = rem < (int64_t)te ? (int)rem : te;
+    const T* gsrc = geo + tile * (int64_t)te * kGeo;
+    T* gdst = geo_s + (size_t)stage * te * kGeo;
+    const int nchunk = ne * kGeo / V;
+    for (int k = threadIdx.x; k < nchunk; k += blockDim.x) cp_async16(gdst + k * V, gsrc + k * V);
+  };
+  auto issue_x = [&](int stage_meta, int stage_x) {
+    const unsigned char* mb = meta + (size_t)stage_meta * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    T* dst = xs + (size_t)stage_x * nnmax * VR;
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      cp_async16(dst + ln * VR + q * V, x + (int64_t)ids[ln] * VR + q * V);
+    }
+  };
+
+  issue_meta(t, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue_x(0, 0);
+  if (t + G < n_tiles) issue_meta(t + G, 1);
+  cp_async_commit();
+
+  for (int i = 0; t < n_tiles; ++i, t += G) {
+    const int ms = i % 3, xb = i & 1;
+    cp_async_wait_all();
+    __syncthreads();
+    const unsigned char* mb = meta + (size_t)ms * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int ne = reinterpret_cast<const int*>(mb)[1];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    const unsigned char* mks = mb + L.mask;
+    const unsigned char* own = mb + L.own;
+    const uint16_t* is = reinterpret_cast<const uint16_t*>(mb + L.inc_start);
+    const uint16_t* lc = reinterpret_cast<const uint16_t*>(mb + L.lconn);
+    const uint16_t* ic = reinterpret_cast<const uint16_t*>(mb + L.inc);
+    const T* gs = geo_s + (size_t)ms * te * kGeo;
+    T* xcur = xs + (size_t)xb * nnmax * VR;
+    // constrained components of the inputs are zero (P x)
+    for (int ln = threadIdx.x; ln < nn; ln += blockDim.x) {
+      const int mk = mks[ln];
+      if (mk != 7)
+        for (int w = 0; w < VR; ++w)
+          if (!((mk >> (w % 3)) & 1)) xcur[ln * VR + w] = T(0);
+    }
+    // offsets: slot of each (element, node) incidence in ob, row of each element node in xs
+    for (int j = threadIdx.x; j < ne * 10; j += blockDim.x) {
+      const int code = ic[j];
+      const int le = code / 10;
+      io[j] = le * S + (code - 10 * le) * VR;
+      const int e = j / 10;
+      no[e * 12 + (j - 10 * e)] = lc[j] * VR;
+    }
+    // prefetch: inputs of the next tile, packet and geometry of the one after
+    if (t + G < n_tiles) issue_x((i + 1) % 3, (i + 1) & 1);
+    if (t + 2 * G < n_tiles) issue_meta(t + 2 * G, (i + 2) % 3);
+    cp_async_commit();
+    __syncthreads();
+
+    // phase 2: element products into their slots
+    for (int it = threadIdx.x; it < ne * R; it += blockDim.x) {
+      const int le = it / R;
+      const int r = it - le * R;
+      ElemGeo<T> Gm;
+      T gv[kGeo];
+#pragma unroll
+      for (int q = 0; q < kGeo / V; ++q) {
+        const VT w = reinterpret_cast<const VT*>(gs + le * kGeo)[q];
+#pragma unroll
+        for (int t2 = 0; t2 < V; ++t2) gv[q * V + t2] = vget(w, t2);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Gm.g[k][d] = gv[3 * k + d];
+      Gm.lam = gv[12];
+      Gm.mu = gv[13];
+      Gm.c = gv[14];
+      int off[12];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int4 w = reinterpret_cast<const int4*>(no + le * 12)[q];
+        off[4 * q] = w.x;
+        off[4 * q + 1] = w.y;
+        off[4 * q + 2] = w.z;
+        off[4 * q + 3] = w.w;
+      }
+      T u[10][3];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        const T* xa = xcur + off[a] + 3 * r;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[a][c] = xa[c];
+      }
+      T yl[10][3];
+      elem_apply(Gm, u, yl);
+      T* o = ob + le * S + 3 * r;
+#pragma unroll
+      for (int a = 0; a < 10; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[a * VR + c] = yl[a][c];
+    }
+    __syncthreads();
+
+    // phase 3: node sums, one 16-byte atomic per 16 bytes of free values
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      VT acc;
+      vzero(acc);
+      const int j1 = is[ln + 1];
+      const T* obq = ob + q * V;
+      for (int j = is[ln]; j < j1; ++j) vadd(acc, *reinterpret_cast<const VT*>(obq + io[j]));
+      const int64_t gi = (int64_t)ids[ln] * VR + q * V;
+      const int mk = mks[ln];
+      if (mk == 7) {
+        vred(reinterpret_cast<VT*>(y + gi), acc);
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < V; ++tt) {
+          if ((mk >> ((q * V + tt) % 3)) & 1)
+            atomicAdd(y + gi + tt, vget(acc, tt));
+          else if (own[ln])
+            y[gi + tt] = __ldg(x + gi + tt);
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 size_t tiled_smem_bytes(int max_nodes, int tile_elems, int R) {
   size_t b = (size_t)max_nodes * 3 * R * sizeof(T) * 2 + (size_t)tile_elems * kGeo * sizeof(T) +
@@ -243,13 +711,104 @@ static int max_smem_optin(int device) {
   return v;
 }
 
-bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32) {
+bool gather_supported(int R) { return R == 1 || R == 2 || R == 3 || R == 4 || R == 8 || R == 16 || R == 32; }
+
+template <typename T>
+static size_t gather_bytes(int R, int nn, int te) {
+  switch (R) {
+    case 1: return gather_smem_bytes<T, 1>(nn, te);
+    case 2: return gather_smem_bytes<T, 2>(nn, te);
+    case 3: return gather_smem_bytes<T, 3>(nn, te);
+    case 4: return gather_smem_bytes<T, 4>(nn, te);
+    case 8: return gather_smem_bytes<T, 8>(nn, te);
+    case 16: return gather_smem_bytes<T, 16>(nn, te);
+    case 32: return gather_smem_bytes<T, 32>(nn, te);
+    default: return (size_t)1 << 40;
+  }
+}
+
+bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind) {
   auto it = m->tilings.find(tile_elems);
   // before the tiling exists, bound its node count by 10 nodes per element
   const int nodes = it != m->tilings.end() ? it->second->max_nodes : 10 * tile_elems;
-  const size_t smem =
-      is_f32 ? tiled_smem_bytes<float>(nodes, tile_elems, R) : tiled_smem_bytes<double>(nodes, tile_elems, R);
+  size_t smem;
+  if (kind == FE_EBE_GATHER)
+    smem = is_f32 ? gather_bytes<float>(R, nodes, tile_elems) : gather_bytes<double>(R, nodes, tile_elems);
+  else
+    smem = is_f32 ? tiled_smem_bytes<float>(nodes, tile_elems, R) : tiled_smem_bytes<double>(nodes, tile_elems, R);
   return smem <= (size_t)max_smem_optin(m->device);
+}
+
+template <typename T, int R>
+static void launch_gather_r(const fe_mesh* m, const Tiling& t, const T* x, T* y, cudaStream_t s, const int* skip) {
+  const size_t smem = gather_smem_bytes<T, R>(t.max_nodes, t.tile_elems);
+  FE_REQUIRE(smem <= (size_t)max_smem_optin(m->device), "gather tile of %d elements needs %zu B shared memory",
+             t.tile_elems, smem);
+  FE_CUDA(cudaFuncSetAttribute(ebe_gather_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ebe_gather_kernel<T, R><<<(unsigned)t.n_tiles, kThreads, smem, s>>>(
+      m->view<T>(), t.tile_elems, t.node_ptr.as<int32_t>(), t.node_ids.as<int32_t>(), t.node_own.as<uint8_t>(),
+      t.lconn.as<uint16_t>(), t.inc.as<uint16_t>(), t.inc_start.as<uint16_t>(), x, y, skip);
+  FE_CHECK_LAUNCH();
+}
+
+template <typename T, int R>
+static bool launch_pipe_r(const fe_mesh* m, const Tiling& t, const T* x, T* y, cudaStream_t s, const int* skip) {
+  if constexpr (!GatherCfg<T, R>::VEC) {
+    return false;
+  } else {
+    const DevBuf& gb = sizeof(T) == 4 ? m->geo32 : m->geo64;
+    if (!gb.ptr || t.packet_bytes == 0) return false;
+    const size_t smem = pipe_smem_bytes<T, R>(t.max_nodes, t.tile_elems, t.packet_bytes);
+    if (smem > (size_t)max_smem_optin(m->device)) return false;
+    FE_CUDA(cudaFuncSetAttribute(ebe_pipe_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one thread per element-case item of a full tile (FP32), in whole warps
+    int threads = kThreads;
+    if (sizeof(T) == 4) {
+      threads = ((t.tile_elems * R + 31) / 32) * 32;
+      threads = threads < 128 ? 128 : (threads > PipeThreads<T>::value ? PipeThreads<T>::value : threads);
+    }
+    int per_sm = 0, sms = 0;
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_pipe_kernel<T, R>, threads, smem));
+    FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    if (per_sm < 1) return false;
+    const int64_t nv = m->n_nodes * (int64_t)R * 3;
+    prep_kernel<T><<<(unsigned)(sms * 8), kThreads, 0, s>>>(m->view<T>(), gb.as<T>(), nv, y, skip);
+    FE_CHECK_LAUNCH();
+    const int64_t grid = std::min<int64_t>(t.n_tiles, (int64_t)per_sm * sms);
+    ebe_pipe_kernel<T, R><<<(unsigned)grid, threads, smem, s>>>(t.n_tiles, m->n_elem, t.tile_elems, t.max_nodes,
+                                                                  t.packets.as<unsigned char>(), t.packet_bytes,
+                                                                  gb.as<T>(), x, y, skip);
+    FE_CHECK_LAUNCH();
+    return true;
+  }
+}
+
+template <typename T>
+static bool launch_pipe(const fe_mesh* m, const Tiling& t, int R, const T* x, T* y, cudaStream_t s,
+                        const int* skip) {
+  switch (R) {
+    case 4: return launch_pipe_r<T, 4>(m, t, x, y, s, skip);
+    case 8: return launch_pipe_r<T, 8>(m, t, x, y, s, skip);
+    case 16: return launch_pipe_r<T, 16>(m, t, x, y, s, skip);
+    case 32: return launch_pipe_r<T, 32>(m, t, x, y, s, skip);
+    case 2: return launch_pipe_r<T, 2>(m, t, x, y, s, skip);
+    default: return false;
+  }
+}
+
+template <typename T>
+static void launch_gather(const fe_mesh* m, const Tiling& t, int R, const T* x, T* y, cudaStream_t s,
+                          const int* skip) {
+  switch (R) {
+    case 1: return launch_gather_r<T, 1>(m, t, x, y, s, skip);
+    case 2: return launch_gather_r<T, 2>(m, t, x, y, s, skip);
+    case 3: return launch_gather_r<T, 3>(m, t, x, y, s, skip);
+    case 4: return launch_gather_r<T, 4>(m, t, x, y, s, skip);
+    case 8: return launch_gather_r<T, 8>(m, t, x, y, s, skip);
+    case 16: return launch_gather_r<T, 16>(m, t, x, y, s, skip);
+    case 32: return launch_gather_r<T, 32>(m, t, x, y, s, skip);
+    default: FE_REQUIRE(false, "gather kernel not compiled for R = %d", R);
+  }
 }
 
 template <typename T>
@@ -271,12 +830,10 @@ int ebe_get_variant(const fe_mesh* m, int R, int is_f32) {
   return v < 0 ? 0 : v;
 }
 
-void ebe_set_variant(fe_mesh* m, int R, int is_f32, int variant) {
-  m->variant[is_f32 ? 1 : 0][R] = (int16_t)variant;
-}
+void ebe_set_variant(fe_mesh* m, int R, int is_f32, int variant) { m->variant[is_f32 ? 1 : 0][R] = variant; }
 
 template <typename T>
-void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip) {
+static void zero_pass(const fe_mesh* m, int R, T* y, cudaStream_t s, const int* skip) {
   const int64_t nv = m->n_nodes * (int64_t)R * 3;
   int sms = 0;
   FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
@@ -284,14 +841,32 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
   zero_kernel<T><<<(unsigned)(zb < (int64_t)sms * 16 ? (zb > 0 ? zb : 1) : (int64_t)sms * 16), kThreads, 0, s>>>(
       nv, y, skip);
   FE_CHECK_LAUNCH();
+}
+
+template <typename T>
+void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip) {
   const int v = ebe_get_variant(m, R, sizeof(T) == 4);
-  if (v > 0) {
-    auto it = m->tilings.find(v);
-    FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", v);
-    launch_tiled<T>(m, *it->second, R, x, y, s, skip);
+  const int kind = v / 65536, tile = v % 65536;
+  if (kind != FE_EBE_DIRECT) {
+    auto it = m->tilings.find(tile);
+    FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
+    if (kind == FE_EBE_GATHER) {
+      if (launch_pipe<T>(m, *it->second, R, x, y, s, skip)) return;
+      zero_pass<T>(m, R, y, s, skip);
+      launch_gather<T>(m, *it->second, R, x, y, s, skip);
+    } else {
+      zero_pass<T>(m, R, y, s, skip);
+      launch_tiled<T>(m, *it->second, R, x, y, s, skip);
+    }
     return;
   }
+  zero_pass<T>(m, R, y, s, skip);
   launch_direct<T>(m, R, x, y, s, skip);
+}
+
+void ensure_geometry_buffer(fe_mesh* m, int is_f32) {
+  DevBuf& b = is_f32 ? m->geo32 : m->geo64;
+  if (!b.ptr) b.alloc((size_t)m->n_elem * kGeo * (is_f32 ? sizeof(float) : sizeof(double)));
 }
 
 template void ebe_apply<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
@@ -312,15 +887,19 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   FE_CUDA(cudaEventCreate(&e0));
   FE_CUDA(cudaEventCreate(&e1));
   std::vector<int> cands = {0};
-  for (int te : {24, 48, 96, 192, 384})
-    if (tiled_fits(m, te, R, sizeof(T) == 4)) cands.push_back(te);
+  for (int te : {12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+    if (gather_supported(R) && tiled_fits(m, te, R, sizeof(T) == 4, FE_EBE_GATHER))
+      cands.push_back(FE_EBE_GATHER * 65536 + te);
+  for (int te : {24, 48, 96})
+    if (tiled_fits(m, te, R, sizeof(T) == 4, FE_EBE_TILED)) cands.push_back(FE_EBE_TILED * 65536 + te);
   *best_variant = 0;
   *best_ms = 1e30f;
   const int old = m->variant[sizeof(T) == 4][R];
+  ensure_geometry_buffer(m, sizeof(T) == 4);
   for (int v : cands) {
     if (v > 0) {
-      get_tiling(m, v, s);
-      if (!tiled_fits(m, v, R, sizeof(T) == 4)) continue;
+      get_tiling(m, v % 65536, s);
+      if (!tiled_fits(m, v % 65536, R, sizeof(T) == 4, v / 65536)) continue;
     }
     ebe_set_variant(m, R, sizeof(T) == 4, v);
     for (int i = 0; i < 2; ++i) ebe_apply<T>(m, R, xb.as<T>(), yb.as<T>(), s);
@@ -336,7 +915,7 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
       *best_variant = v;
     }
   }
-  m->variant[sizeof(T) == 4][R] = (int16_t)old;
+  m->variant[sizeof(T) == 4][R] = old;
   ebe_set_variant(m, R, sizeof(T) == 4, *best_variant);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -86,6 +86,30 @@ struct Tiling {
   DevBuf node_ids;        // int32 [sum of tile node counts] global node ids per tile
   DevBuf node_own;        // uint8, parallel to node_ids: 1 if this is the node's first tile
   DevBuf lconn;           // uint16 [E][10] tile-local node index per element corner
+  DevBuf inc;             // uint16 [E][10] per tile: element-node slots (le*10 + a) sorted by local node
+  DevBuf inc_start;       // uint16, parallel to node_ids: first slot of the node in `inc` (tile-relative)
+  // per-tile packets for the pipelined gather kernel: every array of one tile in
+  // one contiguous block of `packet_bytes` (see PacketLayout)
+  int packet_bytes = 0;
+  DevBuf packets;
+};
+
+// Byte layout of a tile packet (host and device agree on it):
+//   int32 {nn, ne, 0, 0} | int32 ids[nnmax] | uint8 mask[nnmax] | uint8 own[nnmax] |
+//   uint16 inc_start[nnmax + 1] | uint16 lconn[te * 10] | uint16 inc[te * 10]
+// each section padded to 16 bytes.
+struct PacketLayout {
+  int ids, mask, own, inc_start, lconn, inc, bytes;
+  __host__ __device__ static int a16(int b) { return (b + 15) & ~15; }
+  __host__ __device__ PacketLayout(int nnmax, int te) {
+    ids = 16;
+    mask = ids + a16(4 * nnmax);
+    own = mask + a16(nnmax);
+    inc_start = own + a16(nnmax);
+    lconn = inc_start + a16(2 * (nnmax + 1));
+    inc = lconn + a16(20 * te);
+    bytes = inc + a16(20 * te);
+  }
 };
 
 struct SolverWork;  // defined in fe_solver.cu
@@ -110,15 +134,19 @@ struct fe_mesh {
   fe::DevBuf binv32;    // float [N][9]
   // element tilings for the shared-memory EBE kernel, by elements per tile (built lazily)
   std::map<int, std::unique_ptr<fe::Tiling>> tilings;
-  // EBE kernel per precision (0 = FP64, 1 = FP32) and R: -1 = default,
-  // 0 = direct, > 0 = tiled with that many elements per tile
-  int16_t variant[2][65];
+  // EBE kernel per precision (0 = FP64, 1 = FP32) and R: -1 = default, else
+  // kind * 65536 + elements per tile (kind: fe_ebe_variant)
+  int32_t variant[2][65];
   // internal element order -> caller's element id (elements are stored in a
   // locality-preserving order)
   std::vector<int64_t> perm_host;
   fe::DevBuf perm;      // int64 [E]
   fe::DevBuf own_elem;  // uint16 [E]: bit a set if element e is the first element holding its node a
+  // per-product element geometry (g[4][3], lam, mu, V/20, pad) written by the
+  // pipelined kernel's prep pass, FP64 and FP32 (allocated when that kernel is chosen)
+  fe::DevBuf geo64, geo32;
   std::vector<int32_t> conn_host;  // [E][10] in internal order
+  std::vector<uint8_t> nmask_host; // [N] free-DOF bits
   // solver workspace (allocated lazily per R)
   fe::SolverWork* work = nullptr;
 
@@ -134,12 +162,14 @@ namespace fe {
 template <typename T>
 void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip = nullptr);
 
-// kernel choice: 0 = direct, > 0 = tiled with that tile size
+// kernel choice, encoded kind * 65536 + tile (kind: fe_ebe_variant)
 int ebe_get_variant(const fe_mesh* m, int R, int is_f32);
 void ebe_set_variant(fe_mesh* m, int R, int is_f32, int variant);
+bool gather_supported(int R);
+void ensure_geometry_buffer(fe_mesh* m, int is_f32);
 const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
 // largest tile (elements) whose shared-memory footprint fits for (R, precision)
-bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32);
+bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);
 
 // Block Jacobi (fe_solver.cu)
 void build_block_jacobi(fe_mesh* m, cudaStream_t s);

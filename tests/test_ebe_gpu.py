@@ -58,7 +58,7 @@ def mesh_pair(request):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("R", [1, 3, 4, 16, 32])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_ebe_fp64_matches_oracle(mesh_pair, R, variant):
     m, K, M = mesh_pair
     x = mg.random_vectors(m.n_nodes, R, seed=100 + R)
@@ -69,7 +69,7 @@ def test_ebe_fp64_matches_oracle(mesh_pair, R, variant):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("R", [1, 3, 4, 16, 32])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_ebe_fp32_matches_oracle(mesh_pair, R, variant):
     m, K, M = mesh_pair
     x = mg.random_vectors(m.n_nodes, R, seed=200 + R).astype(np.float32).astype(np.float64)
@@ -79,15 +79,37 @@ def test_ebe_fp32_matches_oracle(mesh_pair, R, variant):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("tile", [1, 7, 24, 96, 384])
-def test_tiled_tile_sizes_and_ragged_tail(tile):
+def test_tiled_tile_sizes_and_ragged_tail(tile, variant):
     m = MESHES["ragged"]()
     K = oracle.assemble(m)
     M = gpu_mesh(m)
     x = mg.random_vectors(m.n_nodes, 4, seed=9)
-    y = run(M, x, torch.float64, 1, tile=tile)
+    y = run(M, x, torch.float64, variant, tile=tile)
     assert rel_l2(y, oracle.spmv(K, x)) <= TOL64
-    assert M.get_variant(4, "f64") == (1, tile)
+    kind, used = M.get_variant(4, "f64")
+    assert kind == variant and 1 <= used <= tile      # the largest fitting tile <= the request
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = run(M, x32, torch.float32, variant, tile=tile)
+    assert rel_l2(y32, oracle.spmv(K, x32)) <= TOL32
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R,dtype", [(16, "f32"), (4, "f32"), (32, "f32"), (4, "f64"), (16, "f64")])
+def test_gather_many_tiles_per_cta(R, dtype):
+    """Small tiles on a 24,000-element crust block: thousands of tiles, so every
+    persistent CTA walks many tiles through the prefetch pipeline."""
+    m, _ = mg.crust_block(shape=(20, 20, 10), h=1000.0, jitter=0.15, seed=5)
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, R, seed=31)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    for tile in (4, 13):
+        y = run(M, x, tdt, 2, tile=tile)
+        assert rel_l2(y, oracle.spmv(K, x)) <= (TOL32 if dtype == "f32" else TOL64)
 
 
 @pytest.mark.gpu
