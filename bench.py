@@ -44,10 +44,25 @@ def parse():
     ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
     ap.add_argument("--profile", action="store_true",
                     help="EBE timing only, kernel fixed by --variant/--tile (no tuning, e2e, sweep, solve, CPU)")
-    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather"], help="kernel for --profile")
+    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather", "df"],
+                    help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
     return ap.parse_args()
+
+
+def aggregate(units_per_rank: float, elapsed_ms: float, dist=None, device=None):
+    """Whole-job throughput of a case-sharded run: every rank did `units_per_rank`
+    units; the job took as long as the slowest rank. Returns (units/s over all
+    ranks, max elapsed ms). With `dist` (torch.distributed, initialised) the max
+    is taken over ranks; this is the only collective and it is not on the data path."""
+    import torch
+    world = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return units_per_rank * world / (tmax * 1e-3), tmax
 
 
 def dist_env():
@@ -261,7 +276,7 @@ def run_ours(args):
     M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
     R = R_MAIN
     if args.profile:
-        M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2}[args.variant], args.tile)
+        M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2, "df": 3}[args.variant], args.tile)
         tt = torch.float32 if args.dtype == "f32" else torch.float64
         x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R)).to("cuda", tt)
         y = torch.empty_like(x)
@@ -270,7 +285,7 @@ def run_ours(args):
                           "ms_per_product": ms / args.steps, "per_step_ms": per}), flush=True)
         return
     v32, us32 = M.tune(R, "f32")
-    kind_name = {0: "direct", 1: "tiled", 2: "gather"}[v32 // 65536]
+    kind_name = {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df"}[v32 // 65536]
     kernel_desc = kind_name + ("" if v32 // 65536 == 0 else " %d elements/tile" % (v32 % 65536))
     x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R + rank).astype(np.float32)).cuda()
     y = torch.empty_like(x)
@@ -284,12 +299,8 @@ def run_ours(args):
     time.sleep(0.3)
     total_ms, per = time_ebe(M, x, y, args.steps, args.warmup, torch)
     clocks = sampler.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    units = 3.0 * N * R * args.steps * world
-    value = units / (total_ms * 1e-3) / 1e9
+    rate, total_ms = aggregate(3.0 * N * R * args.steps, total_ms, dist if world > 1 else None, "cuda")
+    value = rate / 1e9
     ms_step = total_ms / args.steps
     ebe_ms = float(np.mean(per))
 
@@ -358,7 +369,7 @@ def run_ours(args):
                 n = 5 if dt == "f64" else 10
                 kv, kt = M.get_variant(RR, dt)
                 sweep[f"{dt}_R{RR}"] = {"GDOF_cases_per_s": 3.0 * N * RR / (ms / n * 1e-3) / 1e9,
-                                        "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather"}[kv],
+                                        "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df"}[kv],
                                         "tile": kt}
                 del xx, yy
         out["ebe_sweep"] = sweep

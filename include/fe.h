@@ -152,8 +152,13 @@ fe_status fe_ebe_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const voi
  *                  element-case product is written to its own shared-memory slot,
  *                  then each tile node sums the slots of its incident elements
  *                  and issues one 16-byte global atomic add per 16 bytes of
- *                  values (R in {1, 2, 3, 4, 8, 16, 32}). */
-typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1, FE_EBE_GATHER = 2 } fe_ebe_variant;
+ *                  values (R in {1, 2, 3, 4, 8, 16, 32});
+ *   FE_EBE_GATHER_DF  FP64 products only (R in {2, 4, 8, 16, 32}): the gather
+ *                  kernel with the element arithmetic and node sums in float-float
+ *                  (pairs of FP32 values, about 48 significant bits) on the FP32
+ *                  pipe, FP64 inputs, outputs and atomics; GB300 runs FP64
+ *                  arithmetic at 1/61 of its FP32 rate. */
+typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1, FE_EBE_GATHER = 2, FE_EBE_GATHER_DF = 3 } fe_ebe_variant;
 
 /*
  * fe_ebe_set_variant -- choose the kernel fe_ebe_apply (and the solvers) use for
@@ -194,6 +199,28 @@ fe_status fe_ebe_tune(fe_mesh* mesh, int32_t R, fe_dtype dtype, void* stream, in
  */
 fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* f_dev, double* u_dev,
                        const fe_solve_opts* opts, fe_solve_stats* stats, void* stream);
+
+/*
+ * fe_solve_many -- solve K_bc u_c = f_c for n_cases load cases with at most R
+ * cases in flight (the many-case workload of Sec. 5, where Green's functions of
+ * hundreds of unit slips are computed in batches). The cases stream through R
+ * slots of one batched solve: when a case converges (or stops), its solution is
+ * stored and its slot is refilled with the next pending case between two outer
+ * iterations, so one slow case does not hold back a whole batch.
+ *   f_dev    device double [n_cases][N][3] (case-major), read only
+ *   u_dev    device double [n_cases][N][3], out (every case starts from u = 0)
+ *   R_slots  cases in flight, 1..64; 0 = choose from free device memory: the
+ *            largest of 32, 16, 8, 4, 2, 1 whose solver vectors fit in 70 % of it
+ *   opts     as fe_pcg_solve (NULL = defaults)
+ *   stats    host [n_cases], per case
+ *   R_used   host, receives the slot count used (may be NULL)
+ * Synchronous. Tunes the EBE kernels for R (FP32 and FP64) and for the single-
+ * case FP64 true-residual product on first use. Allocates two [N][R][3] slot
+ * buffers plus the solver workspace. Returns FE_OK when every case converged,
+ * else FE_ENOCONV or FE_EBREAKDOWN (per-case status in stats).
+ */
+fe_status fe_solve_many(const fe_mesh* mesh, int32_t n_cases, const double* f_dev, double* u_dev, int32_t R_slots,
+                        const fe_solve_opts* opts, fe_solve_stats* stats, int32_t* R_used, void* stream);
 
 /*
  * fe_block_jacobi -- the 3x3 block-Jacobi preconditioner M^-1 = diag3x3[K_bc]^-1

@@ -47,7 +47,13 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
+        _lib = configure(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    if True:
         lib.oracle_tet10_stiffness.argtypes = [_f64p, ctypes.c_double, ctypes.c_double, _f64p]
         lib.oracle_pattern.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i64p, _i32p]
         lib.oracle_pattern.restype = ctypes.c_int64
@@ -67,8 +73,7 @@ def _load():
         lib.oracle_adjoint_grad.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p, _u8p,
                                             ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+    return lib
 
 
 def _p(a: np.ndarray, t):

@@ -144,11 +144,31 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
     buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
     FE_REQUIRE(buf.size() <= 65535 && (e1 - e0) * 10 <= 65535, "tile too large");
     max_nodes = std::max(max_nodes, (int)buf.size());
-    for (int64_t e = e0; e < e1; ++e)
-      for (int a = 0; a < 10; ++a) {
-        const int32_t g = m->conn_host[(size_t)(10 * e + a)];
-        lconn[(size_t)(10 * e + a)] = (uint16_t)(std::lower_bound(buf.begin(), buf.end(), g) - buf.begin());
+    // tile-local node order: most incident elements first, so that the lanes of a
+    // warp that sum node contributions run loops of similar length
+    {
+      const int nb = (int)buf.size();
+      std::vector<int> cnt((size_t)nb, 0), slot((size_t)(e1 - e0) * 10);
+      for (int64_t e = e0; e < e1; ++e)
+        for (int a = 0; a < 10; ++a) {
+          const int32_t g = m->conn_host[(size_t)(10 * e + a)];
+          const int k = (int)(std::lower_bound(buf.begin(), buf.end(), g) - buf.begin());
+          slot[(size_t)((e - e0) * 10 + a)] = k;
+          cnt[(size_t)k]++;
+        }
+      std::vector<int> order((size_t)nb), newpos((size_t)nb);
+      std::iota(order.begin(), order.end(), 0);
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[(size_t)a] > cnt[(size_t)b]; });
+      std::vector<int32_t> sorted((size_t)nb);
+      for (int i = 0; i < nb; ++i) {
+        newpos[(size_t)order[(size_t)i]] = i;
+        sorted[(size_t)i] = buf[(size_t)order[(size_t)i]];
       }
+      buf.swap(sorted);
+      for (int64_t e = e0; e < e1; ++e)
+        for (int a = 0; a < 10; ++a)
+          lconn[(size_t)(10 * e + a)] = (uint16_t)newpos[(size_t)slot[(size_t)((e - e0) * 10 + a)]];
+    }
     FE_REQUIRE(ids.size() + buf.size() < (size_t)INT32_MAX, "tiling too large");
     ids.insert(ids.end(), buf.begin(), buf.end());
     for (int32_t g : buf) {
@@ -418,8 +438,11 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
   return guarded([&] {
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
-    FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER,
+    FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
+                   variant == FE_EBE_GATHER_DF,
                "unknown variant %d", variant);
+    FE_REQUIRE(variant != FE_EBE_GATHER_DF || (dtype == FE_F64 && df_supported(R)),
+               "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
     DeviceGuard dg(m->device);
     if (variant == FE_EBE_DIRECT) {
       ebe_set_variant(m, R, dtype == FE_F32, 0);
@@ -428,9 +451,13 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),
                "the gather kernel is compiled for R in {1, 2, 3, 4, 8, 16, 32}, not %d", R);
     get_tiling(m, tile_elems, (cudaStream_t)stream);
-    if (variant == FE_EBE_GATHER) ensure_geometry_buffer(m, dtype == FE_F32);
-    FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32, variant),
-               "tile of %d elements does not fit in shared memory for R = %d", tile_elems, R);
+    if (variant == FE_EBE_GATHER || variant == FE_EBE_GATHER_DF) ensure_geometry_buffer(m, dtype == FE_F32);
+    if (variant == FE_EBE_GATHER_DF)
+      FE_REQUIRE(df_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",
+                 tile_elems, R);
+    else
+      FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32, variant),
+                 "tile of %d elements does not fit in shared memory for R = %d", tile_elems, R);
     ebe_set_variant(m, R, dtype == FE_F32, variant * 65536 + tile_elems);
   });
 }

@@ -22,9 +22,9 @@ struct df {
   float hi, lo;
   __host__ __device__ df() : hi(0.f), lo(0.f) {}
   __host__ __device__ explicit df(float h, float l) : hi(h), lo(l) {}
-  // small constants of the element code (exact in float)
-  __host__ __device__ df(int v) : hi((float)v), lo(0.f) {}
-  __host__ __device__ df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  // small constants of the element code (0, 2, 3, 4, 0.25: exact in float)
+  __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ constexpr df(double v) : hi((float)v), lo(0.f) {}
 };
 
 __device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
@@ -58,12 +58,49 @@ __device__ __forceinline__ df& operator+=(df& a, const df& b) {
   return a;
 }
 
-// exact split of a double into float-float (hi = RN(x), lo = RN(x - hi))
-__device__ __forceinline__ df df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return df(h, __double2float_rn(x - (double)h));
+// Double -> float-float with integer operations only. (On GB300 the double to
+// float conversion and double additions run at the FP64 rate, 1/61 of FP32.)
+// hi: the double rounded to 24 significant bits (round half away from zero, by
+// adding half a unit of the 24th bit to the bit pattern and truncating; a carry
+// into the exponent is the correct rounding); lo: the remaining x - hi, counted
+// in units of the double's last place and scaled back. |x| below 2^-74 keeps lo = 0
+// (an error below 2^-98 absolute); zero, infinities and NaN map to hi = (float)x.
+__device__ __forceinline__ df df_split(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long mag = b & 0x7FFFFFFFFFFFFFFFLL;
+  const int e = (int)(mag >> 52);                                  // biased double exponent
+  if (e < 1023 - 126 || e > 1023 + 127) return df(__double2float_rn(x), 0.f);  // rare: out of float range
+  const long long rmag = (mag + (1LL << 28)) & ~((1LL << 29) - 1);  // magnitude rounded to 24 bits
+  const int re = (int)(rmag >> 52);
+  if (re > 1023 + 127) return df(__double2float_rn(x), 0.f);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  const float hi = __int_as_float((int)(sign | (unsigned)((re - 1023 + 127) << 23) |
+                                        (unsigned)((rmag >> 29) & 0x7FFFFF)));
+  float lo = 0.f;
+  if (e >= 1023 - 74) {
+    const int d = (int)(mag - rmag);                                 // ulps of x's binade, |d| <= 2^28
+    const float ulp = __int_as_float((e - 1023 - 52 + 127) << 23);   // 2^(e - 1075), a normal float
+    lo = (float)d * ulp;
+    if (sign) lo = -lo;
+  }
+  return df(hi, lo);
 }
 
-__device__ __forceinline__ double df_to_double(const df& a) { return (double)a.hi + (double)a.lo; }
+// Float-float -> double: (double)hi (a fast conversion) plus lo counted in units
+// of that double's last place, added to its bit pattern. If the sum crosses into
+// another binade the exact double addition is used instead (rare).
+__device__ __forceinline__ double df_to_double(const df& a) {
+  const double d = (double)a.hi;
+  if (a.lo == 0.f) return d;
+  const int eh = (int)((__float_as_uint(a.hi) >> 23) & 0xFF);       // biased float exponent of hi
+  // the ulp of d is 2^(eh - 127 - 52); its inverse 2^(179 - eh) is a normal float for eh >= 52
+  if (eh < 52 || eh == 255) return d + (double)a.lo;
+  const float scale = __int_as_float((306 - eh) << 23);
+  const int k = __float2int_rn(a.lo * scale);
+  const long long db = __double_as_longlong(d);
+  const long long rb = db + (a.hi < 0.f ? -(long long)k : (long long)k);
+  if ((rb >> 52) != (db >> 52)) return d + (double)a.lo;
+  return __longlong_as_double(rb);
+}
 
 }  // namespace fe

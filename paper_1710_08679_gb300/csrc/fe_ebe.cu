@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "fe_df.cuh"
 #include "fe_element.cuh"
 #include "fe_internal.cuh"
 
@@ -669,7 +670,22 @@ __global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t
       vzero(acc);
       const int j1 = is[ln + 1];
       const T* obq = ob + q * V;
-      for (int j = is[ln]; j < j1; ++j) vadd(acc, *reinterpret_cast<const VT*>(obq + io[j]));
+      int j = is[ln];
+      VT acc1;
+      vzero(acc1);
+      for (; j + 3 < j1; j += 4) {   // four independent loads in flight
+        const int o0 = io[j], o1 = io[j + 1], o2 = io[j + 2], o3 = io[j + 3];
+        const VT v0 = *reinterpret_cast<const VT*>(obq + o0);
+        const VT v1 = *reinterpret_cast<const VT*>(obq + o1);
+        const VT v2 = *reinterpret_cast<const VT*>(obq + o2);
+        const VT v3 = *reinterpret_cast<const VT*>(obq + o3);
+        vadd(acc, v0);
+        vadd(acc1, v1);
+        vadd(acc, v2);
+        vadd(acc1, v3);
+      }
+      for (; j < j1; ++j) vadd(acc, *reinterpret_cast<const VT*>(obq + io[j]));
+      vadd(acc, acc1);
       const int64_t gi = (int64_t)ids[ln] * VR + q * V;
       const int mk = mks[ln];
       if (mk == 7) {
@@ -682,6 +698,207 @@ __global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t
           else if (own[ln])
             y[gi + tt] = __ldg(x + gi + tt);
         }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64-accurate pipelined gather kernel in float-float arithmetic.
+// Same tiles, packets and phases as ebe_pipe_kernel<double>, but the element
+// products and the node sums run on the FP32 pipe in float-float (fe_df.cuh):
+// the prep pass computes the geometry in FP64 and splits it into float-float,
+// phase 1 splits the gathered FP64 inputs in place (integer operations), and
+// phase 3 converts each node sum back to FP64 before its atomic add.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) prep_df_kernel(MeshView<double> M, df* __restrict__ geo, int64_t nv,
+                                                           double* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t e = gid; e < M.n_elem; e += stride) {
+    int nd[10];
+    load_conn<double>(M.conn, e, nd);
+    ElemGeo<double> G;
+    load_geometry(M, e, nd, G);
+    double v[kGeo];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[3 * k + i] = G.g[k][i];
+    v[12] = G.lam;
+    v[13] = G.mu;
+    v[14] = G.c;
+    v[15] = 0.0;
+    float4* dst = reinterpret_cast<float4*>(geo + e * kGeo);
+#pragma unroll
+    for (int q = 0; q < kGeo / 2; ++q) {
+      const df a = df_split(v[2 * q]), b = df_split(v[2 * q + 1]);
+      dst[q] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+  }
+  const int64_t n16 = nv / 2;
+  for (int64_t i = gid; i < n16; i += stride) reinterpret_cast<double2*>(y)[i] = make_double2(0.0, 0.0);
+  for (int64_t i = n16 * 2 + gid; i < nv; i += stride) y[i] = 0.0;
+}
+
+template <int R>
+__host__ __device__ size_t pipe_df_smem_bytes(int nnmax, int te, int pk) {
+  // same carve-up as the FP64 kernel: float-float values are 8 bytes like doubles
+  return pipe_smem_bytes<double, R>(nnmax, te, pk);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) ebe_pipe_df_kernel(int64_t n_tiles, int64_t n_elem, int te, int nnmax,
+                                                               const unsigned char* __restrict__ packets, int pk,
+                                                               const df* __restrict__ geo, const double* __restrict__ x,
+                                                               double* __restrict__ y, const int* __restrict__ skip) {
+  using C = GatherCfg<double, R>;
+  constexpr int VR = C::VR, S = C::S, CPN = VR / 2;   // 16-byte chunks of two values
+  static_assert(C::VEC, "float-float kernel needs 16-byte node rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (skip && *skip) return;
+  const PacketLayout L(nnmax, te);
+  unsigned char* meta = smem_raw;                                   // [3][pk]
+  df* geo_s = reinterpret_cast<df*>(meta + 3 * (size_t)pk);         // [3][te][16]
+  double* xs = reinterpret_cast<double*>(geo_s + 3 * (size_t)te * kGeo);  // [2][nnmax][VR], split in place
+  df* ob = reinterpret_cast<df*>(xs + 2 * (size_t)nnmax * VR);      // [te][S]
+  int* io = reinterpret_cast<int*>(ob + (size_t)te * S);            // [te*10]
+  int* no = io + ((te * 10 + 3) & ~3);                              // [te][12]
+  const int64_t G = gridDim.x;
+  int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+
+  auto issue_meta = [&](int64_t tile, int stage) {
+    const unsigned char* src = packets + tile * (int64_t)pk;
+    unsigned char* dst = meta + (size_t)stage * pk;
+    for (int k = threadIdx.x; k < pk / 16; k += blockDim.x) cp_async16(dst + 16 * k, src + 16 * k);
+    const int64_t rem = n_elem - tile * (int64_t)te;
+    const int ne = rem < (int64_t)te ? (int)rem : te;
+    const df* gsrc = geo + tile * (int64_t)te * kGeo;
+    df* gdst = geo_s + (size_t)stage * te * kGeo;
+    for (int k = threadIdx.x; k < ne * kGeo / 2; k += blockDim.x) cp_async16(gdst + 2 * k, gsrc + 2 * k);
+  };
+  auto issue_x = [&](int stage_meta, int stage_x) {
+    const unsigned char* mb = meta + (size_t)stage_meta * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    double* dst = xs + (size_t)stage_x * nnmax * VR;
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      cp_async16(dst + ln * VR + 2 * q, x + (int64_t)ids[ln] * VR + 2 * q);
+    }
+  };
+
+  issue_meta(t, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue_x(0, 0);
+  if (t + G < n_tiles) issue_meta(t + G, 1);
+  cp_async_commit();
+
+  for (int i = 0; t < n_tiles; ++i, t += G) {
+    const int ms = i % 3, xb = i & 1;
+    cp_async_wait_all();
+    __syncthreads();
+    const unsigned char* mb = meta + (size_t)ms * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int ne = reinterpret_cast<const int*>(mb)[1];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    const unsigned char* mks = mb + L.mask;
+    const unsigned char* own = mb + L.own;
+    const uint16_t* is = reinterpret_cast<const uint16_t*>(mb + L.inc_start);
+    const uint16_t* lc = reinterpret_cast<const uint16_t*>(mb + L.lconn);
+    const uint16_t* ic = reinterpret_cast<const uint16_t*>(mb + L.inc);
+    const df* gs = geo_s + (size_t)ms * te * kGeo;
+    double* xd = xs + (size_t)xb * nnmax * VR;
+    df* xcur = reinterpret_cast<df*>(xd);
+    // split the inputs in place (P x: constrained components become zero)
+    for (int k = threadIdx.x; k < nn * VR; k += blockDim.x) {
+      const int ln = k / VR;
+      const int w = k - ln * VR;
+      const double v = xd[k];
+      xcur[k] = ((mks[ln] >> (w % 3)) & 1) ? df_split(v) : df(0.f, 0.f);
+    }
+    for (int j = threadIdx.x; j < ne * 10; j += blockDim.x) {
+      const int code = ic[j];
+      const int le = code / 10;
+      io[j] = le * S + (code - 10 * le) * VR;
+      const int e = j / 10;
+      no[e * 12 + (j - 10 * e)] = lc[j] * VR;
+    }
+    if (t + G < n_tiles) issue_x((i + 1) % 3, (i + 1) & 1);
+    if (t + 2 * G < n_tiles) issue_meta(t + 2 * G, (i + 2) % 3);
+    cp_async_commit();
+    __syncthreads();
+
+    for (int it = threadIdx.x; it < ne * R; it += blockDim.x) {
+      const int le = it / R;
+      const int r = it - le * R;
+      ElemGeo<df> Gm;
+      df gv[kGeo];
+#pragma unroll
+      for (int q = 0; q < kGeo / 2; ++q) {
+        const float4 w = reinterpret_cast<const float4*>(gs + le * kGeo)[q];
+        gv[2 * q] = df(w.x, w.y);
+        gv[2 * q + 1] = df(w.z, w.w);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Gm.g[k][d] = gv[3 * k + d];
+      Gm.lam = gv[12];
+      Gm.mu = gv[13];
+      Gm.c = gv[14];
+      int off[12];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int4 w = reinterpret_cast<const int4*>(no + le * 12)[q];
+        off[4 * q] = w.x;
+        off[4 * q + 1] = w.y;
+        off[4 * q + 2] = w.z;
+        off[4 * q + 3] = w.w;
+      }
+      df u[10][3];
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        const df* xa = xcur + off[a] + 3 * r;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[a][c] = xa[c];
+      }
+      df yl[10][3];
+      elem_apply(Gm, u, yl);
+      df* o = ob + le * S + 3 * r;
+#pragma unroll
+      for (int a = 0; a < 10; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[a * VR + c] = yl[a][c];
+    }
+    __syncthreads();
+
+    // node sums in float-float, converted to FP64 for the global atomic add
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      df a0, a1;
+      const int j1 = is[ln + 1];
+      const df* obq = ob + 2 * q;
+      for (int j = is[ln]; j < j1; ++j) {
+        const float4 w = *reinterpret_cast<const float4*>(obq + io[j]);
+        a0 += df(w.x, w.y);
+        a1 += df(w.z, w.w);
+      }
+      const int64_t gi = (int64_t)ids[ln] * VR + 2 * q;
+      const int mk = mks[ln];
+      const df acc[2] = {a0, a1};
+#pragma unroll
+      for (int tt = 0; tt < 2; ++tt) {
+        if ((mk >> ((2 * q + tt) % 3)) & 1)
+          atomicAdd(y + gi + tt, df_to_double(acc[tt]));
+        else if (own[ln])
+          y[gi + tt] = __ldg(x + gi + tt);
       }
     }
   }
@@ -783,6 +1000,40 @@ static bool launch_pipe_r(const fe_mesh* m, const Tiling& t, const T* x, T* y, c
   }
 }
 
+template <int R>
+static bool launch_pipe_df_r(const fe_mesh* m, const Tiling& t, const double* x, double* y, cudaStream_t s,
+                             const int* skip) {
+  if (!m->geodf.ptr || t.packet_bytes == 0) return false;
+  const size_t smem = pipe_df_smem_bytes<R>(t.max_nodes, t.tile_elems, t.packet_bytes);
+  if (smem > (size_t)max_smem_optin(m->device)) return false;
+  FE_CUDA(cudaFuncSetAttribute(ebe_pipe_df_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_pipe_df_kernel<R>, kThreads, smem));
+  FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+  if (per_sm < 1) return false;
+  const int64_t nv = m->n_nodes * (int64_t)R * 3;
+  prep_df_kernel<<<(unsigned)(sms * 8), kThreads, 0, s>>>(m->view<double>(), m->geodf.as<df>(), nv, y, skip);
+  FE_CHECK_LAUNCH();
+  const int64_t grid = std::min<int64_t>(t.n_tiles, (int64_t)per_sm * sms);
+  ebe_pipe_df_kernel<R><<<(unsigned)grid, kThreads, smem, s>>>(t.n_tiles, m->n_elem, t.tile_elems, t.max_nodes,
+                                                               t.packets.as<unsigned char>(), t.packet_bytes,
+                                                               m->geodf.as<df>(), x, y, skip);
+  FE_CHECK_LAUNCH();
+  return true;
+}
+
+static bool launch_pipe_df(const fe_mesh* m, const Tiling& t, int R, const double* x, double* y, cudaStream_t s,
+                           const int* skip) {
+  switch (R) {
+    case 2: return launch_pipe_df_r<2>(m, t, x, y, s, skip);
+    case 4: return launch_pipe_df_r<4>(m, t, x, y, s, skip);
+    case 8: return launch_pipe_df_r<8>(m, t, x, y, s, skip);
+    case 16: return launch_pipe_df_r<16>(m, t, x, y, s, skip);
+    case 32: return launch_pipe_df_r<32>(m, t, x, y, s, skip);
+    default: return false;
+  }
+}
+
 template <typename T>
 static bool launch_pipe(const fe_mesh* m, const Tiling& t, int R, const T* x, T* y, cudaStream_t s,
                         const int* skip) {
@@ -850,7 +1101,12 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
   if (kind != FE_EBE_DIRECT) {
     auto it = m->tilings.find(tile);
     FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
-    if (kind == FE_EBE_GATHER) {
+    if (kind == FE_EBE_GATHER_DF) {
+      FE_REQUIRE(sizeof(T) == 8, "the float-float kernel computes FP64 products only");
+      FE_REQUIRE(launch_pipe_df(m, *it->second, R, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
+                                s, skip),
+                 "float-float kernel unavailable for R = %d with tiles of %d elements", R, tile);
+    } else if (kind == FE_EBE_GATHER) {
       if (launch_pipe<T>(m, *it->second, R, x, y, s, skip)) return;
       zero_pass<T>(m, R, y, s, skip);
       launch_gather<T>(m, *it->second, R, x, y, s, skip);
@@ -867,6 +1123,25 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
 void ensure_geometry_buffer(fe_mesh* m, int is_f32) {
   DevBuf& b = is_f32 ? m->geo32 : m->geo64;
   if (!b.ptr) b.alloc((size_t)m->n_elem * kGeo * (is_f32 ? sizeof(float) : sizeof(double)));
+  if (!is_f32 && !m->geodf.ptr) m->geodf.alloc((size_t)m->n_elem * kGeo * sizeof(df));
+}
+
+bool df_supported(int R) { return R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
+
+bool df_fits(const fe_mesh* m, int tile_elems, int R) {
+  auto it = m->tilings.find(tile_elems);
+  if (it == m->tilings.end()) return false;
+  const Tiling& t = *it->second;
+  size_t smem;
+  switch (R) {
+    case 2: smem = pipe_df_smem_bytes<2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 4: smem = pipe_df_smem_bytes<4>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 8: smem = pipe_df_smem_bytes<8>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 16: smem = pipe_df_smem_bytes<16>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 32: smem = pipe_df_smem_bytes<32>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    default: return false;
+  }
+  return smem <= (size_t)max_smem_optin(m->device);
 }
 
 template void ebe_apply<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
@@ -892,6 +1167,9 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
       cands.push_back(FE_EBE_GATHER * 65536 + te);
   for (int te : {24, 48, 96})
     if (tiled_fits(m, te, R, sizeof(T) == 4, FE_EBE_TILED)) cands.push_back(FE_EBE_TILED * 65536 + te);
+  if (sizeof(T) == 8 && df_supported(R))
+    for (int te : {4, 8, 12, 16, 24})
+      if (tiled_fits(m, te, R, 0, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_DF * 65536 + te);
   *best_variant = 0;
   *best_ms = 1e30f;
   const int old = m->variant[sizeof(T) == 4][R];
@@ -899,7 +1177,11 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   for (int v : cands) {
     if (v > 0) {
       get_tiling(m, v % 65536, s);
-      if (!tiled_fits(m, v % 65536, R, sizeof(T) == 4, v / 65536)) continue;
+      if (v / 65536 == FE_EBE_GATHER_DF) {
+        if (!df_fits(m, v % 65536, R)) continue;
+      } else if (!tiled_fits(m, v % 65536, R, sizeof(T) == 4, v / 65536)) {
+        continue;
+      }
     }
     ebe_set_variant(m, R, sizeof(T) == 4, v);
     for (int i = 0; i < 2; ++i) ebe_apply<T>(m, R, xb.as<T>(), yb.as<T>(), s);

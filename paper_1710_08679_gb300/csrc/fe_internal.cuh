@@ -145,6 +145,7 @@ struct fe_mesh {
   // per-product element geometry (g[4][3], lam, mu, V/20, pad) written by the
   // pipelined kernel's prep pass, FP64 and FP32 (allocated when that kernel is chosen)
   fe::DevBuf geo64, geo32;
+  fe::DevBuf geodf;     // float-float geometry [E][16] for the float-float FP64 kernel
   std::vector<int32_t> conn_host;  // [E][10] in internal order
   std::vector<uint8_t> nmask_host; // [N] free-DOF bits
   // solver workspace (allocated lazily per R)
@@ -167,6 +168,8 @@ int ebe_get_variant(const fe_mesh* m, int R, int is_f32);
 void ebe_set_variant(fe_mesh* m, int R, int is_f32, int variant);
 bool gather_supported(int R);
 void ensure_geometry_buffer(fe_mesh* m, int is_f32);
+bool df_supported(int R);
+bool df_fits(const fe_mesh* m, int tile_elems, int R);
 const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
 // largest tile (elements) whose shared-memory footprint fits for (R, precision)
 bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);

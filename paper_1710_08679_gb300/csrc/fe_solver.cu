@@ -17,6 +17,7 @@
 // neighbouring addresses. Dot products accumulate per thread (FP32 products in
 // FP32 for the inner loop, FP64 otherwise), then per block in FP64 shared
 // memory, then with one FP64 atomic add per block and case.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -522,6 +523,66 @@ __global__ void k_case_resid(int64_t N, int R, int c, const uint8_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// slot management of the many-case driver
+// ---------------------------------------------------------------------------
+// slot r <- case: F[:, r, :] = f_case, U[:, r, :] = 0 (f_case is [N][3])
+__global__ void k_load_case(int64_t N, int R, int r, const double* __restrict__ fc, double* __restrict__ F,
+                            double* __restrict__ U) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  for (int k = 0; k < 3; ++k) {
+    F[(n * R + r) * 3 + k] = fc[3 * n + k];
+    U[(n * R + r) * 3 + k] = 0.0;
+  }
+}
+
+// u_case <- U[:, r, :]
+__global__ void k_store_case(int64_t N, int R, int r, const double* __restrict__ U, double* __restrict__ uc) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  for (int k = 0; k < 3; ++k) uc[3 * n + k] = U[(n * R + r) * 3 + k];
+}
+
+// slot r starts from u = 0: r = P f, ||P f||^2 into fn2 and rn2 (both zeroed before)
+__global__ void k_slot_init(int64_t N, int R, int r, const uint8_t* __restrict__ nmask, const double* __restrict__ F,
+                            double* __restrict__ rv, double* __restrict__ fn2, double* __restrict__ rn2) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const int mk = nmask[n];
+    for (int k = 0; k < 3; ++k) {
+      const int64_t o = (n * R + r) * 3 + k;
+      const double v = ((mk >> k) & 1) ? F[o] : 0.0;
+      rv[o] = v;
+      acc += v * v;
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(fn2, sm[0]);
+    atomicAdd(rn2, sm[0]);
+  }
+}
+
+// per-case state of a freshly loaded slot (one thread)
+__global__ void s_slot_start(Cases C, int r, int pcg) {
+  const bool zero = !(C.D(D_FN2, r) > 0.0);
+  C.I(I_ACTIVE, r) = zero ? 0 : 1;
+  C.I(I_CAND, r) = 0;
+  C.I(I_RESTART, r) = (!zero && pcg) ? 1 : 0;   // PCG: p and rho from r at the next restart pass
+  C.I(I_FIRST, r) = 1;
+  C.I(I_STATUS, r) = FE_OK;
+  C.I(I_OUTER, r) = 0;
+  C.I(I_INNER, r) = 0;
+  C.D(D_RELRES, r) = 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // per-case scalar kernels (one block of R threads)
 // ---------------------------------------------------------------------------
 __global__ void s_init(Cases C) {
@@ -814,8 +875,20 @@ static void pcg_iteration(Solve& S) {
   S.vec(k_pcg_p, B64, (const double*)w->r.as<double>(), w->p.as<double>());
 }
 
+// Many-case mode: n_cases right-hand sides stream through R slots. f and u of
+// run_solve are then the slot buffers; a slot whose case finished is stored to
+// u_all and refilled with the next pending case between two iterations.
+struct Many {
+  int n_cases = 0;
+  const double* f_all = nullptr;   // [n_cases][N][3]
+  double* u_all = nullptr;         // [n_cases][N][3]
+  fe_solve_stats* stats = nullptr; // [n_cases]
+  int next = 0;
+  std::vector<int> slot_case;      // [R], -1 = idle
+};
+
 static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const fe_solve_opts& o,
-                           fe_solve_stats* stats, cudaStream_t user) {
+                           fe_solve_stats* stats, cudaStream_t user, Many* many = nullptr) {
   SolverWork* w = get_work(m, R);
   cudaStream_t s = w->stream;
   // order after the caller's pending work on `user`
@@ -838,6 +911,17 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   S.o = o;
   const bool pcg = o.solver == FE_SOLVER_PCG64;
 
+  if (many) {
+    // the first R cases into the slots (idle slots hold f = 0 and stay inactive)
+    FE_CUDA(cudaMemsetAsync(const_cast<double*>(f), 0, (size_t)S.N * R * 3 * sizeof(double), s));
+    many->slot_case.assign((size_t)R, -1);
+    for (int r = 0; r < R && many->next < many->n_cases; ++r, ++many->next) {
+      k_load_case<<<(unsigned)((S.N + 255) / 256), 256, 0, s>>>(S.N, R, r, many->f_all + (size_t)many->next * S.N * 3,
+                                                               const_cast<double*>(f), u);
+      FE_CHECK_LAUNCH();
+      many->slot_case[(size_t)r] = many->next;
+    }
+  }
   // start: u = P u, r = P f - K u, ||f||, ||r||
   S.scal(s_init);
   S.vec(k_prepare, m->nmask.as<uint8_t>(), f, u);
@@ -897,8 +981,49 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
         }
         if (hi[I_ACTIVE * R + c]) any_active = true;
       }
+      if (many) {
+        // finished slots: store the case, refill with the next pending case
+        FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaStreamSynchronize(s));
+        for (int r = 0; r < R; ++r) {
+          const int cs = many->slot_case[(size_t)r];
+          if (cs < 0 || hi[I_ACTIVE * R + r] || hi[I_CAND * R + r]) continue;
+          const int st = hi[I_STATUS * R + r];
+          double rel = hd[D_RELRES * R + r];
+          if (st != FE_OK) rel = S.true_relres(r, hd[D_FN2 * R + r], false);
+          k_store_case<<<(unsigned)((S.N + 255) / 256), 256, 0, s>>>(S.N, R, r, u, many->u_all + (size_t)cs * S.N * 3);
+          FE_CHECK_LAUNCH();
+          if (many->stats) {
+            many->stats[cs].outer_iters = hi[I_OUTER * R + r];
+            many->stats[cs].inner_iters = hi[I_INNER * R + r];
+            many->stats[cs].relres = rel;
+            many->stats[cs].status = st;
+            many->stats[cs].pad = 0;
+          }
+          if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
+          else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
+          many->slot_case[(size_t)r] = -1;
+          if (many->next < many->n_cases) {
+            const int nc = many->next++;
+            k_load_case<<<(unsigned)((S.N + 255) / 256), 256, 0, s>>>(S.N, R, r, many->f_all + (size_t)nc * S.N * 3,
+                                                                     const_cast<double*>(f), u);
+            FE_CHECK_LAUNCH();
+            FE_CUDA(cudaMemsetAsync(w->d.as<double>() + D_FN2 * R + r, 0, 8, s));
+            FE_CUDA(cudaMemsetAsync(w->d.as<double>() + D_RN2 * R + r, 0, 8, s));
+            k_slot_init<<<(unsigned)std::min<int64_t>((S.N + 255) / 256, 1024), 256, 0, s>>>(
+                S.N, R, r, m->nmask.as<uint8_t>(), f, w->r.as<double>(), w->d.as<double>() + D_FN2 * R + r,
+                w->d.as<double>() + D_RN2 * R + r);
+            FE_CHECK_LAUNCH();
+            s_slot_start<<<1, 1, 0, s>>>(S.C, r, pcg ? 1 : 0);
+            FE_CHECK_LAUNCH();
+            many->slot_case[(size_t)r] = nc;
+            any_active = true;
+          }
+        }
+      }
       if (pcg) {
-        // cases whose recursive residual drifted restart CG from their true residual
+        // cases whose recursive residual drifted (or freshly loaded slots) restart CG from r
         FE_CUDA(cudaMemsetAsync(w->d.as<double>() + D_RHOA * R, 0, R * 8, s));
         S.vec(k_pcg_restart, m->binv64.as<double>(), (const double*)w->r.as<double>(), w->p.as<double>());
         S.scal(s_pcg_restart);
@@ -917,7 +1042,7 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
     FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
-    for (int c = 0; c < R; ++c) {
+    for (int c = 0; c < R && !many; ++c) {
       int st = hi[I_STATUS * R + c];
       double rel = hd[D_RELRES * R + c];
       if (st != FE_OK) rel = S.true_relres(c, hd[D_FN2 * R + c], false);
@@ -964,6 +1089,73 @@ extern "C" fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* 
     fe_mesh* m = const_cast<fe_mesh*>(mesh);
     fe::DeviceGuard dg(m->device);
     return fe::run_solve(m, R, f, u, o, stats, (cudaStream_t)stream);
+  } catch (const fe::Failure& x) {
+    return x.status;
+  } catch (...) {
+    fe::set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}
+
+namespace fe {
+
+// free device memory -> slot count (largest of 32, 16, 8, 4, 2, 1 that fits with a margin)
+static int choose_slots(const fe_mesh* m, int n_cases) {
+  size_t free_b = 0, total_b = 0;
+  FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  // per slot: FP64 F, U, r, p, q and FP32 rbar, ubar, e, pbar, qbar vectors of [N][3]
+  const double per_slot = (double)m->n_nodes * 3 * (5 * 8 + 5 * 4);
+  const double budget = 0.7 * (double)free_b;
+  int R = 32;
+  while (R > 1 && (R > n_cases || R * per_slot > budget)) R /= 2;
+  return R;
+}
+
+// kernels for the products a solve with R slots runs, tuned on first use
+static void tune_if_unset(fe_mesh* m, int R, cudaStream_t s) {
+  int32_t v = 0, us = 0;
+  const int todo[3][2] = {{R, FE_F32}, {R, FE_F64}, {1, FE_F64}};
+  for (const auto& t : todo) {
+    if (m->variant[t[1] == FE_F32 ? 1 : 0][t[0]] >= 0) continue;
+    const fe_status st = fe_ebe_tune(m, t[0], (fe_dtype)t[1], s, &v, &us);
+    if (st != FE_OK) throw Failure{st};
+  }
+}
+
+}  // namespace fe
+
+extern "C" fe_status fe_solve_many(const fe_mesh* mesh, int32_t n_cases, const double* f_dev, double* u_dev,
+                                   int32_t R_slots, const fe_solve_opts* opts, fe_solve_stats* stats, int32_t* R_used,
+                                   void* stream) {
+  try {
+    fe::clear_error();
+    FE_REQUIRE(mesh != nullptr, "mesh is NULL");
+    FE_REQUIRE(n_cases >= 1, "n_cases must be >= 1");
+    FE_REQUIRE(f_dev != nullptr && u_dev != nullptr, "NULL vector");
+    FE_REQUIRE(R_slots >= 0 && R_slots <= 64, "R_slots = %d out of range [0, 64]", R_slots);
+    fe_solve_opts o;
+    fe_solve_opts_default(&o);
+    if (opts) o = *opts;
+    FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED, "unknown solver %d", o.solver);
+    FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
+    FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
+    FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
+    fe_mesh* m = const_cast<fe_mesh*>(mesh);
+    fe::DeviceGuard dg(m->device);
+    const int R = R_slots > 0 ? (R_slots < n_cases ? R_slots : n_cases) : fe::choose_slots(m, n_cases);
+    if (R_used) *R_used = R;
+    fe::tune_if_unset(m, R, (cudaStream_t)stream);
+    fe::DevBuf F, U;
+    F.alloc((size_t)m->n_nodes * R * 3 * sizeof(double));
+    U.alloc((size_t)m->n_nodes * R * 3 * sizeof(double));
+    fe::Many many;
+    many.n_cases = n_cases;
+    many.f_all = f_dev;
+    many.u_all = u_dev;
+    many.stats = stats;
+    const fe_status st = fe::run_solve(m, R, F.as<double>(), U.as<double>(), o, nullptr, (cudaStream_t)stream, &many);
+    FE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return st;
   } catch (const fe::Failure& x) {
     return x.status;
   } catch (...) {

@@ -27,8 +27,8 @@ STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "F
 # every symbol include/fe.h declares
 EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_create", "fe_mesh_destroy",
             "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
-            "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_block_jacobi_noalloc",
-            "fe_adjoint_grad"]
+            "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
+            "fe_block_jacobi_noalloc", "fe_adjoint_grad"]
 
 
 class FeError(RuntimeError):
@@ -78,11 +78,13 @@ def load(path: Optional[str] = None):
     lib.fe_ebe_tune.argtypes = [_vp, _i32, _i32, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
     lib.fe_pcg_solve.argtypes = [_vp, _i32, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp]
     lib.fe_adjoint_grad.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
+    lib.fe_solve_many.argtypes = [_vp, _i32, _vp, _vp, _i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats),
+                                  ctypes.POINTER(_i32), _vp]
     lib.fe_block_jacobi.argtypes = [_vp, _vp, _vp]
     lib.fe_block_jacobi_noalloc.argtypes = [_vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
-                 "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_block_jacobi", "fe_block_jacobi_noalloc",
-                 "fe_adjoint_grad"):
+                 "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
+                 "fe_block_jacobi_noalloc", "fe_adjoint_grad"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -234,6 +236,29 @@ class Mesh:
         if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
             _check(st, "fe_pcg_solve")
         return u, out, st
+
+    def solve_many(self, f_cases, R_slots: int = 0, solver: str = "fcg_mixed", tol: float = 1e-8,
+                   max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
+                   raise_on_fail: bool = True):
+        """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
+        in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
+        torch = _torch()
+        n = int(f_cases.shape[0])
+        fp = _dev_ptr(f_cases, torch.float64, (n, self.n_nodes, 3), name="f_cases")
+        u = torch.empty_like(f_cases)
+        o = SolveOpts()
+        load().fe_solve_opts_default(ctypes.byref(o))
+        o.solver = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED}[solver]
+        o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
+        o.use_graph = int(bool(use_graph))
+        stats = (SolveStats * n)()
+        r_used = _i32()
+        st = load().fe_solve_many(self._h, n, fp, ctypes.c_void_p(u.data_ptr()), int(R_slots), ctypes.byref(o),
+                                  stats, ctypes.byref(r_used), self._stream())
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, relres=s.relres, status=s.status) for s in stats]
+        if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
+            _check(st, "fe_solve_many")
+        return u, out, st, r_used.value
 
     def block_jacobi(self):
         """Inverse 3x3 diagonal blocks of K_bc, float64 [N, 3, 3]."""

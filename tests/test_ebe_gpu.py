@@ -113,6 +113,34 @@ def test_gather_many_tiles_per_cta(R, dtype):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("R", [2, 4, 16, 32])
+def test_float_float_fp64_kernel_matches_oracle(mesh_pair, R):
+    """The FP64 product computed in float-float arithmetic on the FP32 pipe meets
+    the FP64 bar (1e-12)."""
+    m, K, M = mesh_pair
+    x = mg.random_vectors(m.n_nodes, R, seed=300 + R)
+    y = run(M, x, torch.float64, 3, tile=16)
+    assert M.get_variant(R, "f64")[0] == 3
+    assert rel_l2(y, oracle.spmv(K, x)) <= TOL64
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [4, 16])
+def test_float_float_many_tiles_and_scales(R):
+    """Many tiles per CTA, and inputs spanning 40 orders of magnitude."""
+    m, _ = mg.crust_block(shape=(20, 20, 10), h=1000.0, jitter=0.15, seed=5)
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    rng = np.random.default_rng(7)
+    x = mg.random_vectors(m.n_nodes, R, seed=32) * 10.0 ** rng.uniform(-20, 20, size=(m.n_nodes, R, 1))
+    for tile in (4, 13):
+        y = run(M, x, torch.float64, 3, tile=tile)
+        y_ref = oracle.spmv(K, x)
+        for r in range(R):
+            assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
+
+
+@pytest.mark.gpu
 def test_batched_equals_separate_products():
     m = MESHES["box8"]()
     M = gpu_mesh(m)
@@ -162,7 +190,11 @@ def test_full_size_crust_block_sampled_rows(dtype):
         x = x.astype(np.float32).astype(np.float64)
     M.tune(R, dtype)
     y = run(M, x, tdt)
+    if dtype == "f64":   # the float-float kernel too, whatever the tuner picked
+        y2 = run(M, x, tdt, 3, tile=16)
     rng = np.random.default_rng(0)
     nodes = np.unique(np.concatenate([rng.integers(0, m.n_nodes, 3000), [0, m.n_nodes - 1]]))
     ys = oracle.sampled_product(m, x, nodes)
     assert rel_l2(y[nodes], ys) <= (TOL64 if dtype == "f64" else TOL32)
+    if dtype == "f64":
+        assert rel_l2(y2[nodes], ys) <= TOL64

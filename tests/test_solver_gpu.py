@@ -174,3 +174,32 @@ def test_set_log_young_changes_operator(box8):
     y = M.ebe(cuda(x)).cpu().numpy()
     K2 = oracle.assemble(m, young=np.exp(le))
     assert rel_l2(y, oracle.spmv(K2, x)) <= 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solver,R_slots", [("fcg_mixed", 4), ("pcg64", 3), ("fcg_mixed", 0)])
+def test_solve_many_streams_cases_through_slots(box8, solver, R_slots):
+    """11 cases (double couples at different places, a zero case, random loads)
+    through at most R_slots slots: every case is solved to 1e-8 and matches the
+    oracle's direct solve; a converged slot is refilled with the next case."""
+    m, K, M = box8
+    lx, ly, lz = m.lattice_shape()
+    cases = []
+    for k in range(8):
+        cases.append(mg.double_couple(m, (lx // 2 - 4 + k, ly // 2 + (k % 3) - 1, lz // 2 + (k % 4)), 1e12))
+    cases.append(np.zeros((m.n_nodes, 3)))
+    rng = np.random.default_rng(4)
+    for k in range(2):
+        cases.append(rng.standard_normal((m.n_nodes, 3)) * 1e9 * m.free)
+    F = np.stack(cases, axis=0)                        # [n_cases, N, 3]
+    u, stats, st, R_used = M.solve_many(cuda(F), R_slots=R_slots, solver=solver, tol=1e-8)
+    assert st == 0, stats
+    assert 1 <= R_used <= (R_slots if R_slots else 32)
+    u = u.cpu().numpy()
+    ud = oracle.direct_solve(K, np.ascontiguousarray(F.transpose(1, 0, 2)))
+    for c in range(F.shape[0]):
+        if c == 8:
+            assert np.all(u[c] == 0.0) and stats[c]["relres"] == 0.0
+            continue
+        assert stats[c]["status"] == 0 and stats[c]["relres"] <= 1e-8, (c, stats[c])
+        assert rel_l2(u[c], ud[:, c]) <= 1e-6, c
