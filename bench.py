@@ -35,7 +35,7 @@ R_MAIN = 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true", help="skip the solve comparison")
@@ -290,8 +290,9 @@ def run_ours(args):
                           "ms_per_product": ms / args.steps, "per_step_ms": per}), flush=True)
         return
     v32, us32 = M.tune(R, "f32")
-    kind_name = {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df"}[v32 // 65536]
+    kind_name = {0: "direct", 1: "tiled", 2: "pipelined gather", 3: "gather-df"}[v32 // 65536]
     kernel_desc = kind_name + ("" if v32 // 65536 == 0 else " %d elements/tile" % (v32 % 65536))
+    first_pass = "prep pass (element geometry, y = 0)" if v32 // 65536 == 2 else "zero pass"
     x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R + rank).astype(np.float32)).cuda()
     y = torch.empty_like(x)
 
@@ -348,7 +349,7 @@ def run_ours(args):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "fe_ebe_apply (zero pass + %s EBE kernel)" % kernel_desc,
+                "kernel": "fe_ebe_apply (%s + %s EBE kernel)" % (first_pass, kernel_desc),
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                         "peak_source": peak_src, "algorithmic_bytes": bytes_alg}}
@@ -360,7 +361,8 @@ def run_ours(args):
                       "mesh_dof": 3 * N, "R": R, "kernel_variant": kernel_desc,
                       "l2": "inputs larger than L2 (x and y %d MB each), no flush" % (x.numel() * 4 // 2 ** 20),
                       "parallelism": "case-sharded replicas x%d" % world},
-           "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "clocks": clocks}
+           "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "clocks": clocks,
+           "profiles": "profiles/ebe_crust70x70x35_R16_fp32_launches.md"}
 
     if not args.no_sweep:
         sweep = {}
