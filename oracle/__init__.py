@@ -73,6 +73,19 @@ def configure(lib):
         lib.oracle_adjoint_grad.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p, _u8p,
                                             ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_pattern_n.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i32p, _i64p, _i32p]
+        lib.oracle_pattern_n.restype = ctypes.c_int64
+        lib.oracle_tet4_stiffness.argtypes = [_f64p, ctypes.c_double, ctypes.c_double, _f64p]
+        lib.oracle_assemble4.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p, _i64p, _i32p,
+                                         _f64p]
+        lib.oracle_prolong.argtypes = [ctypes.c_int64, ctypes.c_int, _i32p, _f64p, _f64p]
+        lib.oracle_prolong.restype = None
+        lib.oracle_restrict.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i32p, _f64p, _f64p]
+        lib.oracle_restrict.restype = None
+        lib.oracle_fcg_mg.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int, _f64p, _f64p,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      _u8p, ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _u8p, _i32p, ctypes.c_int,
+                                      ctypes.c_double, _i32p, _i32p, _i32p, _f64p]
     return lib
 
 
@@ -242,3 +255,132 @@ def direct_solve(K: Assembled, f: np.ndarray) -> np.ndarray:
     rhs = np.ascontiguousarray(np.moveaxis(f, 1, 2)).reshape(3 * N, R)
     sol = lu.solve(rhs)
     return np.ascontiguousarray(np.moveaxis(sol.reshape(N, 3, R), 2, 1))
+
+
+# ---------------------------------------------------------------------------
+# first-order (TET4) coarse level: the same mesh without edge nodes
+# ---------------------------------------------------------------------------
+
+_EDGES = ((0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3))
+
+
+@dataclass
+class Coarse:
+    """TET4 mesh made of the corner nodes of a TET10 mesh.
+    coords [N4, 3], conn [E, 4], free [N4, 3], young/poisson [E], vertex [N4] (TET10
+    id of each TET4 node), ends [N10, 2] (TET4 nodes whose mean gives each TET10 node)."""
+    coords: np.ndarray
+    conn: np.ndarray
+    young: np.ndarray
+    poisson: np.ndarray
+    free: np.ndarray
+    vertex: np.ndarray
+    ends: np.ndarray
+
+
+def coarse_mesh(mesh) -> Coarse:
+    conn = np.asarray(mesh.conn, dtype=np.int64)
+    vert = np.unique(conn[:, :4])
+    new = -np.ones(np.asarray(mesh.coords).shape[0], dtype=np.int64)
+    new[vert] = np.arange(vert.size)
+    ends = np.zeros((new.size, 2), dtype=np.int32)
+    ends[vert, 0] = new[vert]
+    ends[vert, 1] = new[vert]
+    for q, (a, b) in enumerate(_EDGES):
+        ends[conn[:, 4 + q], 0] = new[conn[:, a]]
+        ends[conn[:, 4 + q], 1] = new[conn[:, b]]
+    return Coarse(coords=np.asarray(mesh.coords)[vert], conn=new[conn[:, :4]].astype(np.int32),
+                  young=np.asarray(mesh.young), poisson=np.asarray(mesh.poisson), free=np.asarray(mesh.free)[vert],
+                  vertex=vert, ends=ends)
+
+
+def tet4_stiffness(xe: np.ndarray, E: float, nu: float) -> np.ndarray:
+    lib = _load()
+    xe = _c(xe, np.float64).reshape(12)
+    Ke = np.zeros(144)
+    if lib.oracle_tet4_stiffness(_p(xe, _f64p), float(E), float(nu), _p(Ke, _f64p)) != 0:
+        raise ValueError("non-positive element Jacobian")
+    return Ke.reshape(12, 12)
+
+
+def assemble4(coarse: Coarse, apply_bc: bool = True, young=None) -> Assembled:
+    lib = _load()
+    coords, conn = _c(coarse.coords, np.float64), _c(coarse.conn, np.int32)
+    E = _c(coarse.young if young is None else young, np.float64)
+    nu = _c(coarse.poisson, np.float64)
+    N, Ne = coords.shape[0], conn.shape[0]
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    nnzb = lib.oracle_pattern_n(N, Ne, 4, _p(conn, _i32p), _p(rowptr, _i64p), None)
+    if nnzb < 0:
+        raise ValueError("bad connectivity")
+    col = np.zeros(nnzb, dtype=np.int32)
+    lib.oracle_pattern_n(N, Ne, 4, _p(conn, _i32p), _p(rowptr, _i64p), _p(col, _i32p))
+    vals = np.zeros((nnzb, 3, 3))
+    if lib.oracle_assemble4(N, _p(coords, _f64p), Ne, _p(conn, _i32p), _p(E, _f64p), _p(nu, _f64p),
+                            _p(rowptr, _i64p), _p(col, _i32p), _p(vals, _f64p)) != 0:
+        raise ValueError("assembly failed")
+    if apply_bc:
+        free = _c(coarse.free, np.uint8)
+        lib.oracle_apply_bc(N, _p(rowptr, _i64p), _p(col, _i32p), _p(vals, _f64p), _p(free, _u8p))
+    return Assembled(N, rowptr, col, vals)
+
+
+def prolong(coarse: Coarse, u4: np.ndarray) -> np.ndarray:
+    """u10 = P1 u4 ([N4, R, 3] -> [N10, R, 3])."""
+    lib = _load()
+    u4 = _c(u4, np.float64)
+    R = u4.shape[1]
+    N10 = coarse.ends.shape[0]
+    out = np.zeros((N10, R, 3))
+    ends = _c(coarse.ends, np.int32)
+    lib.oracle_prolong(N10, R, _p(ends, _i32p), _p(u4, _f64p), _p(out, _f64p))
+    return out
+
+
+def restrict(coarse: Coarse, r10: np.ndarray) -> np.ndarray:
+    """r4 = P1^T r10 ([N10, R, 3] -> [N4, R, 3])."""
+    lib = _load()
+    r10 = _c(r10, np.float64)
+    R = r10.shape[1]
+    N10, N4 = coarse.ends.shape[0], coarse.coords.shape[0]
+    out = np.zeros((N4, R, 3))
+    ends = _c(coarse.ends, np.int32)
+    lib.oracle_restrict(N10, N4, R, _p(ends, _i32p), _p(r10, _f64p), _p(out, _f64p))
+    return out
+
+
+def fcg_mg(K: Assembled, f: np.ndarray, coarse: Coarse = None, K1: Assembled = None, free=None, u0=None,
+           tol: float = 1e-8,
+           max_outer: int = 10000, n_inner: int = 30, eps_inner: float = 0.1, n_inner1: int = 300,
+           eps_inner1: float = 0.05, literal_beta: bool = False):
+    """Flexible CG with the FP32 inner loop at level 0 and, with `coarse`, the TET4
+    level 1 before it: (u, outer, inner0_total, inner1_total, relres)."""
+    lib = _load()
+    f = _c(f, np.float64)
+    R = f.shape[1]
+    u = np.zeros_like(f) if u0 is None else _c(u0, np.float64).copy()
+    Minv = block_jacobi(K)
+    outer = np.zeros(R, dtype=np.int32)
+    inner = np.zeros(R, dtype=np.int32)
+    inner1 = np.zeros(R, dtype=np.int32)
+    rel = np.zeros(R)
+    if coarse is not None:
+        if K1 is None:
+            K1 = assemble4(coarse)
+        Minv1 = block_jacobi(K1)
+        ends = _c(coarse.ends, np.int32)
+        free4 = _c(coarse.free, np.uint8)
+        if free is None:
+            raise ValueError("the free mask of the fine mesh is needed with a coarse level")
+        free10 = _c(free, np.uint8)
+        args1 = (_p(free10, _u8p), K1.n_nodes, _p(K1.rowptr, _i64p), _p(K1.col, _i32p), _p(K1.vals, _f64p),
+                 _p(Minv1, _f64p), _p(free4, _u8p), _p(ends, _i32p), int(n_inner1), float(eps_inner1))
+    else:
+        args1 = (None, 0, None, None, None, None, None, None, 0, 0.0)
+    rc = lib.oracle_fcg_mg(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p), _p(Minv, _f64p), R,
+                           _p(f, _f64p), _p(u, _f64p), float(tol), int(max_outer), int(n_inner), float(eps_inner),
+                           int(bool(literal_beta)), *args1, _p(outer, _i32p), _p(inner, _i32p), _p(inner1, _i32p),
+                           _p(rel, _f64p))
+    if rc != 0:
+        raise RuntimeError("fcg_mg failed (%d)" % rc)
+    return u, outer, inner, inner1, rel

@@ -165,20 +165,20 @@ static int cmp_i32(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
-/* node -> element incidence lists (CSR); caller frees *nptr and *nel */
-static int node_elements(int64_t N, int64_t E, const int32_t* conn, int64_t** nptr, int64_t** nel) {
+/* node -> element incidence lists (CSR) for elements of `nen` nodes; caller frees *nptr and *nel */
+static int node_elements_n(int64_t N, int64_t E, int nen, const int32_t* conn, int64_t** nptr, int64_t** nel) {
   int64_t* ptr = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
   if (!ptr) return -2;
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 10; ++a) ptr[conn[10 * e + a] + 1]++;
+    for (int a = 0; a < nen; ++a) ptr[conn[nen * e + a] + 1]++;
   for (int64_t n = 0; n < N; ++n) ptr[n + 1] += ptr[n];
   int64_t* lst = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ptr[N] > 0 ? ptr[N] : 1));
   int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
   if (!lst || !fill) { free(ptr); free(lst); free(fill); return -2; }
   for (int64_t n = 0; n < N; ++n) fill[n] = ptr[n];
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 10; ++a) {
-      int32_t n = conn[10 * e + a];
+    for (int a = 0; a < nen; ++a) {
+      int32_t n = conn[nen * e + a];
       /* an element lists a node once; a repeated node would be a malformed element */
       lst[fill[n]++] = e;
     }
@@ -188,31 +188,38 @@ static int node_elements(int64_t N, int64_t E, const int32_t* conn, int64_t** np
   return 0;
 }
 
-static int check_conn(int64_t N, int64_t E, const int32_t* conn) {
+static int node_elements(int64_t N, int64_t E, const int32_t* conn, int64_t** nptr, int64_t** nel) {
+  return node_elements_n(N, E, 10, conn, nptr, nel);
+}
+
+static int check_conn_n(int64_t N, int64_t E, int nen, const int32_t* conn) {
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 10; ++a) {
-      if (conn[10 * e + a] < 0 || conn[10 * e + a] >= N) return -1;
+    for (int a = 0; a < nen; ++a) {
+      if (conn[nen * e + a] < 0 || conn[nen * e + a] >= N) return -1;
       for (int b = 0; b < a; ++b)
-        if (conn[10 * e + a] == conn[10 * e + b]) return -1;
+        if (conn[nen * e + a] == conn[nen * e + b]) return -1;
     }
   return 0;
 }
 
-/* Block pattern of K: block (n, m) present iff nodes n and m share an element.
- * rowptr[N+1] is always written; col[] (sorted per row) only when col != NULL.
- * Returns the number of blocks, or a negative code. */
-int64_t oracle_pattern(int64_t N, int64_t E, const int32_t* conn, int64_t* rowptr, int32_t* col) {
-  if (N <= 0 || E < 0 || check_conn(N, E, conn)) return -1;
+static int check_conn(int64_t N, int64_t E, const int32_t* conn) { return check_conn_n(N, E, 10, conn); }
+
+/* Block pattern of K for elements of `nen` nodes (10: TET10, 4: TET4): block (n, m)
+ * present iff nodes n and m share an element. rowptr[N+1] is always written; col[]
+ * (sorted per row) only when col != NULL. Returns the number of blocks, or a
+ * negative code. */
+int64_t oracle_pattern_n(int64_t N, int64_t E, int nen, const int32_t* conn, int64_t* rowptr, int32_t* col) {
+  if (N <= 0 || E < 0 || (nen != 4 && nen != 10) || check_conn_n(N, E, nen, conn)) return -1;
   int64_t *nptr, *nel;
-  if (node_elements(N, E, conn, &nptr, &nel)) return -2;
+  if (node_elements_n(N, E, nen, conn, &nptr, &nel)) return -2;
   int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * 4096);
   size_t cap = 4096;
   rowptr[0] = 0;
   for (int64_t n = 0; n < N; ++n) {
     size_t cnt = 0;
     for (int64_t p = nptr[n]; p < nptr[n + 1]; ++p) {
-      if (cnt + 10 > cap) { cap *= 2; buf = (int32_t*)realloc(buf, sizeof(int32_t) * cap); }
-      for (int a = 0; a < 10; ++a) buf[cnt++] = conn[10 * nel[p] + a];
+      if (cnt + (size_t)nen > cap) { cap *= 2; buf = (int32_t*)realloc(buf, sizeof(int32_t) * cap); }
+      for (int a = 0; a < nen; ++a) buf[cnt++] = conn[nen * nel[p] + a];
     }
     if (cnt == 0) buf[cnt++] = (int32_t)n;   /* isolated node keeps its diagonal block */
     qsort(buf, cnt, sizeof(int32_t), cmp_i32);
@@ -226,6 +233,10 @@ int64_t oracle_pattern(int64_t N, int64_t E, const int32_t* conn, int64_t* rowpt
   free(nptr);
   free(nel);
   return rowptr[N];
+}
+
+int64_t oracle_pattern(int64_t N, int64_t E, const int32_t* conn, int64_t* rowptr, int32_t* col) {
+  return oracle_pattern_n(N, E, 10, conn, rowptr, col);
 }
 
 static int64_t find_block(const int64_t* rowptr, const int32_t* col, int32_t n, int32_t m) {
@@ -305,6 +316,133 @@ static void spmv_f32(int64_t N, const int64_t* rowptr, const int32_t* col, const
       for (int i = 0; i < 3; ++i) y[3 * (n * R + r) + i] = acc[i];
     }
   }
+}
+
+/* ------------------------------------------------------------------------- */
+/* first-order (TET4) coarse level of the multigrid inner solve (Sec. 2: the   */
+/* same mesh without edge nodes)                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Ke[12*12] of a 4-node (linear) tetrahedron: K_e = V B^T D B with the constant
+ * B of the linear shape functions N_a = L_a (one-point rule, exact). */
+int oracle_tet4_stiffness(const double* xe, double E, double nu, double* Ke) {
+  static const double dL[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double D[6][6];
+  elasticity_D(E, nu, D);
+  double J[3][3] = {{0}}; /* J[i][k] = dx_i / dxi_k */
+  for (int n = 0; n < 4; ++n)
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) J[i][k] += xe[3 * n + i] * dL[n][k];
+  double Ji[3][3];
+  double det = inv3(J, Ji);
+  if (!(det > 0.0)) return -1;
+  double B[6][12];
+  memset(B, 0, sizeof(B));
+  for (int n = 0; n < 4; ++n) {
+    double g[3];
+    for (int i = 0; i < 3; ++i) g[i] = dL[n][0] * Ji[0][i] + dL[n][1] * Ji[1][i] + dL[n][2] * Ji[2][i];
+    int c = 3 * n;
+    B[0][c + 0] = g[0];
+    B[1][c + 1] = g[1];
+    B[2][c + 2] = g[2];
+    B[3][c + 1] = g[2]; B[3][c + 2] = g[1];
+    B[4][c + 0] = g[2]; B[4][c + 2] = g[0];
+    B[5][c + 0] = g[1]; B[5][c + 1] = g[0];
+  }
+  double V = det / 6.0;
+  for (int r = 0; r < 12; ++r)
+    for (int s = 0; s < 12; ++s) {
+      double acc = 0.0;
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) acc += B[i][r] * D[i][j] * B[j][s];
+      Ke[12 * r + s] = V * acc;
+    }
+  return 0;
+}
+
+/* Assembled K_1 = sum_e Q_e K_e^(4) Q_e^T of a TET4 mesh (coords4 [N4][3], conn4 [E][4]). */
+int oracle_assemble4(int64_t N, const double* coords, int64_t E, const int32_t* conn,
+                     const double* young, const double* poisson,
+                     const int64_t* rowptr, const int32_t* col, double* vals) {
+  memset(vals, 0, sizeof(double) * 9 * (size_t)rowptr[N]);
+  double Ke[144], xe[12];
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t* ce = conn + 4 * e;
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i) xe[3 * a + i] = coords[3 * (int64_t)ce[a] + i];
+    if (oracle_tet4_stiffness(xe, young[e], poisson[e], Ke)) return -1;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        int64_t blk = find_block(rowptr, col, ce[a], ce[b]);
+        if (blk < 0) return -3;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) vals[9 * blk + 3 * i + j] += Ke[12 * (3 * a + i) + 3 * b + j];
+      }
+  }
+  return 0;
+}
+
+/* Mapping between the TET4 and TET10 node sets: ends[2n], ends[2n+1] are the TET4
+ * nodes whose linear interpolation gives TET10 node n (equal for a vertex). */
+/* u10 = P u4 (prolongation: vertices copied, edge nodes the mean of their ends) */
+void oracle_prolong(int64_t N10, int R, const int32_t* ends, const double* u4, double* u10) {
+  for (int64_t n = 0; n < N10; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i) {
+        int32_t a = ends[2 * n], b = ends[2 * n + 1];
+        u10[3 * (n * R + r) + i] = (a == b) ? u4[3 * ((int64_t)a * R + r) + i]
+                                            : 0.5 * (u4[3 * ((int64_t)a * R + r) + i] + u4[3 * ((int64_t)b * R + r) + i]);
+      }
+}
+
+/* r4 = P^T r10 (restriction, the transpose of oracle_prolong) */
+void oracle_restrict(int64_t N10, int64_t N4, int R, const int32_t* ends, const double* r10, double* r4) {
+  memset(r4, 0, sizeof(double) * 3 * (size_t)N4 * R);
+  for (int64_t n = 0; n < N10; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i) {
+        int32_t a = ends[2 * n], b = ends[2 * n + 1];
+        double v = r10[3 * (n * R + r) + i];
+        if (a == b) {
+          r4[3 * ((int64_t)a * R + r) + i] += v;
+        } else {
+          r4[3 * ((int64_t)a * R + r) + i] += 0.5 * v;
+          r4[3 * ((int64_t)b * R + r) + i] += 0.5 * v;
+        }
+      }
+}
+
+static void prolong_f32(int64_t N10, int R, const int32_t* ends, const float* u4, float* u10) {
+  for (int64_t n = 0; n < N10; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i) {
+        int32_t a = ends[2 * n], b = ends[2 * n + 1];
+        u10[3 * (n * R + r) + i] = (a == b) ? u4[3 * ((int64_t)a * R + r) + i]
+                                            : 0.5f * (u4[3 * ((int64_t)a * R + r) + i] + u4[3 * ((int64_t)b * R + r) + i]);
+      }
+}
+
+static void mask_f32(int64_t N, int R, const uint8_t* free_mask, float* v) {
+  for (int64_t n = 0; n < N; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i)
+        if (!free_mask[3 * n + i]) v[3 * (n * R + r) + i] = 0.0f;
+}
+
+static void restrict_f32(int64_t N10, int64_t N4, int R, const int32_t* ends, const float* r10, float* r4) {
+  memset(r4, 0, sizeof(float) * 3 * (size_t)N4 * R);
+  for (int64_t n = 0; n < N10; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i) {
+        int32_t a = ends[2 * n], b = ends[2 * n + 1];
+        float v = r10[3 * (n * R + r) + i];
+        if (a == b) {
+          r4[3 * ((int64_t)a * R + r) + i] += v;
+        } else {
+          r4[3 * ((int64_t)a * R + r) + i] += 0.5f * v;
+          r4[3 * ((int64_t)b * R + r) + i] += 0.5f * v;
+        }
+      }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -472,51 +610,118 @@ int oracle_pcg(int64_t N, const int64_t* rowptr, const int32_t* col, const doubl
 }
 
 /* ------------------------------------------------------------------------- */
-/* Flexible (adaptive) CG, Algorithm 1(a) without levels 1-2, with the FP32   */
-/* inner PCG of Algorithm 1(b) at level 0, R cases at once                    */
+/* Flexible (adaptive) CG, Algorithm 1(a) with level 2 dropped, and the FP32   */
+/* inner PCG of Algorithm 1(b), R cases at once                               */
 /* ------------------------------------------------------------------------- */
 
+/* Algorithm 1(b) on one level, FP32 vectors and products, dots accumulated in FP64:
+ *   e = rb - Kbar ub; while max_r ||e_r||^2/||rb_r||^2 > eps and steps < n_steps:
+ *   z = Mbar^-1 e; rho_a = (z, e); beta = rho_a/rho_b (after the first step);
+ *   p = z + beta p; q = Kbar p; gamma = (p, q); alpha = rho_a/gamma; rho_b = rho_a;
+ *   e -= alpha q; ub += alpha p.
+ * Only cases with active[c] take part (their count of steps goes to steps[c]). */
+static int inner_pcg_f32(int64_t N, const int64_t* rowptr, const int32_t* col, const float* vals32,
+                         const float* Minv32, int R, const float* rb, float* ub, int n_steps, double eps,
+                         const int* active, int32_t* steps) {
+  size_t nv = (size_t)N * R * 3;
+  float *eb = malloc(nv * 4), *zb = malloc(nv * 4), *pb = malloc(nv * 4), *qb = malloc(nv * 4);
+  double *rbn = malloc(R * 8), *en = malloc(R * 8), *rho_a = malloc(R * 8), *rho_b = malloc(R * 8), *gb = malloc(R * 8);
+  if (!eb || !zb || !pb || !qb || !rbn || !en || !rho_a || !rho_b || !gb) return -2;
+  spmv_f32(N, rowptr, col, vals32, R, ub, qb);
+  for (size_t k = 0; k < nv; ++k) eb[k] = rb[k] - qb[k];
+  dots_f32(N, R, rb, rb, rbn);
+  for (int step = 0; step < n_steps; ++step) {
+    dots_f32(N, R, eb, eb, en);
+    double worst = 0.0;
+    for (int c = 0; c < R; ++c)
+      if (active[c] && rbn[c] > 0.0 && en[c] / rbn[c] > worst) worst = en[c] / rbn[c];
+    if (!(worst > eps)) break;
+    apply_blocks_f32(N, R, Minv32, eb, zb);
+    dots_f32(N, R, zb, eb, rho_a);
+    for (int64_t n = 0; n < N; ++n)
+      for (int c = 0; c < R; ++c) {
+        if (!active[c]) continue;
+        float beta = step > 0 ? (float)(rho_a[c] / rho_b[c]) : 0.0f;
+        for (int i = 0; i < 3; ++i) {
+          size_t k = 3 * (n * R + c) + i;
+          pb[k] = zb[k] + beta * (step > 0 ? pb[k] : 0.0f);
+        }
+      }
+    spmv_f32(N, rowptr, col, vals32, R, pb, qb);
+    dots_f32(N, R, pb, qb, gb);
+    for (int64_t n = 0; n < N; ++n)
+      for (int c = 0; c < R; ++c) {
+        if (!active[c]) continue;
+        float alpha = (float)(rho_a[c] / gb[c]);
+        for (int i = 0; i < 3; ++i) {
+          size_t k = 3 * (n * R + c) + i;
+          eb[k] -= alpha * qb[k];
+          ub[k] += alpha * pb[k];
+        }
+      }
+    for (int c = 0; c < R; ++c)
+      if (active[c]) { rho_b[c] = rho_a[c]; steps[c]++; }
+  }
+  free(eb); free(zb); free(pb); free(qb); free(rbn); free(en); free(rho_a); free(rho_b); free(gb);
+  return 0;
+}
+
 /* Outer loop (FP64), per case r while ||r||/||f|| > tol (per-case masking):
- *   rbar = (float) r; ubar = Mbar^-1 rbar; inner loop on Kbar ubar = rbar;
- *   z = (double) ubar;
+ *   rbar = (float) r; ubar = Mbar^-1 rbar                               (lines 9-10)
+ *   with the TET4 level (N4 > 0):
+ *     rbar1 = P1^T rbar; ubar1 = P1^T ubar                              (line 11)
+ *     inner loop (b) on Kbar1 ubar1 = rbar1 with eps_inner1, n_inner1   (line 15)
+ *     ubar = P1 ubar1                                                   (line 16)
+ *   inner loop (b) on Kbar ubar = rbar with eps_inner, n_inner          (line 17)
+ *   z = (double) ubar                                                   (line 18, read as z)
  *   if i > 1: beta = -(z, q_prev) / (p_prev, q_prev)   (flexible CG; the paper
  *             prints gamma=(z,q), beta=gamma/rho, read as this form -- with
- *             literal_beta != 0 the printed form is used instead);
+ *             literal_beta != 0 the printed form is used instead)
  *   p = z + beta p;  q = K p;  rho = (z, r);  gamma = (p, q);  alpha = rho/gamma;
  *   r -= alpha q;  u += alpha p.
- * Inner loop (FP32 vectors and products, dots accumulated in FP64):
- *   e = rbar - Kbar ubar; while max_r ||e_r||^2/||rbar_r||^2 > eps_inner and
- *   steps < n_inner: z = Mbar^-1 e; rho_a = (z, e); beta = rho_a/rho_b (after
- *   the first step); p = z + beta p; q = Kbar p; gamma = (p, q);
- *   alpha = rho_a/gamma; rho_b = rho_a; e -= alpha q; ubar += alpha p.
- * Kbar is K_bc with entries rounded to FP32. Cases whose outer loop has
- * converged are frozen (their inner updates are skipped and they do not count in
- * the inner max). outer[r], inner_total[r], relres[r] (true residual) written. */
-int oracle_fcg_mixed(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
-                     int R, const double* f, double* u, double tol, int max_outer, int n_inner, double eps_inner,
-                     int literal_beta, int32_t* outer, int32_t* inner_total, double* relres) {
-  size_t nv = (size_t)N * R * 3;
+ * Kbar, Kbar1 are K_bc, K1_bc with entries rounded to FP32. Cases whose outer loop
+ * has converged are frozen (they skip the inner loops and do not count in their
+ * max rule). outer[r], inner_total[r] (level 0 steps), inner1_total[r] (level 1
+ * steps), relres[r] (true residual) are written. */
+int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
+                  int R, const double* f, double* u, double tol, int max_outer, int n_inner, double eps_inner,
+                  int literal_beta, const uint8_t* free_mask, int64_t N4, const int64_t* rowptr4,
+                  const int32_t* col4, const double* vals4, const double* Minv4, const uint8_t* free4,
+                  const int32_t* ends, int n_inner1, double eps_inner1,
+                  int32_t* outer, int32_t* inner_total, int32_t* inner1_total, double* relres) {
+  size_t nv = (size_t)N * R * 3, nv4 = (size_t)(N4 > 0 ? N4 : 1) * R * 3;
   int64_t nnzb = rowptr[N];
   float* vals32 = malloc(sizeof(float) * 9 * (size_t)nnzb);
   float* Minv32 = malloc(sizeof(float) * 9 * (size_t)N);
+  float *vals4_32 = NULL, *Minv4_32 = NULL, *rb1 = NULL, *ub1 = NULL;
   double *r = malloc(nv * 8), *z = malloc(nv * 8), *p = malloc(nv * 8), *q = malloc(nv * 8);
-  float *rb = malloc(nv * 4), *ub = malloc(nv * 4), *eb = malloc(nv * 4), *zb = malloc(nv * 4),
-        *pb = malloc(nv * 4), *qb = malloc(nv * 4);
+  float *rb = malloc(nv * 4), *ub = malloc(nv * 4);
   double *fn = malloc(R * 8), *rn = malloc(R * 8), *rho = malloc(R * 8), *gam = malloc(R * 8),
-         *zq = malloc(R * 8), *pq_prev = malloc(R * 8), *rbn = malloc(R * 8), *en = malloc(R * 8),
-         *rho_a = malloc(R * 8), *rho_b = malloc(R * 8), *gb = malloc(R * 8), *rho_prev = malloc(R * 8);
+         *zq = malloc(R * 8), *pq_prev = malloc(R * 8), *rho_prev = malloc(R * 8), *bet = malloc(R * 8);
   int* active = malloc(R * sizeof(int));
-  if (!vals32 || !Minv32 || !r || !z || !p || !q || !rb || !ub || !eb || !zb || !pb || !qb || !fn || !rn ||
-      !rho || !gam || !zq || !pq_prev || !rbn || !en || !rho_a || !rho_b || !gb || !active || !rho_prev)
+  if (!vals32 || !Minv32 || !r || !z || !p || !q || !rb || !ub || !fn || !rn || !rho || !gam || !zq || !pq_prev ||
+      !rho_prev || !bet || !active)
     return -2;
   for (int64_t k = 0; k < 9 * nnzb; ++k) vals32[k] = (float)vals[k];
   for (int64_t k = 0; k < 9 * N; ++k) Minv32[k] = (float)Minv[k];
+  if (N4 > 0) {
+    vals4_32 = malloc(sizeof(float) * 9 * (size_t)rowptr4[N4]);
+    Minv4_32 = malloc(sizeof(float) * 9 * (size_t)N4);
+    rb1 = malloc(nv4 * 4);
+    ub1 = malloc(nv4 * 4);
+    if (!vals4_32 || !Minv4_32 || !rb1 || !ub1) return -2;
+    for (int64_t k = 0; k < 9 * rowptr4[N4]; ++k) vals4_32[k] = (float)vals4[k];
+    for (int64_t k = 0; k < 9 * N4; ++k) Minv4_32[k] = (float)Minv4[k];
+  }
 
   oracle_spmv(N, rowptr, col, vals, R, u, q);            /* lines 4-5: r = f - K u */
   for (size_t k = 0; k < nv; ++k) r[k] = f[k] - q[k];
   memset(p, 0, nv * 8);
   dots(N, R, f, f, fn);
-  for (int c = 0; c < R; ++c) { outer[c] = 0; inner_total[c] = 0; active[c] = fn[c] > 0.0; }
+  for (int c = 0; c < R; ++c) {
+    outer[c] = 0; inner_total[c] = 0; if (inner1_total) inner1_total[c] = 0; active[c] = fn[c] > 0.0;
+  }
+  int rc = 0;
   for (int it = 1; it <= max_outer; ++it) {
     dots(N, R, r, r, rn);
     int any = 0;
@@ -525,55 +730,27 @@ int oracle_fcg_mixed(int64_t N, const int64_t* rowptr, const int32_t* col, const
       any |= active[c];
     }
     if (!any) break;
-    /* lines 9-10: rbar = r; ubar = Mbar^-1 rbar */
     for (size_t k = 0; k < nv; ++k) rb[k] = (float)r[k];
     apply_blocks_f32(N, R, Minv32, rb, ub);
-    /* inner loop (b), level 0 */
-    spmv_f32(N, rowptr, col, vals32, R, ub, qb);
-    for (size_t k = 0; k < nv; ++k) eb[k] = rb[k] - qb[k];
-    dots_f32(N, R, rb, rb, rbn);
-    for (int step = 0; step < n_inner; ++step) {
-      dots_f32(N, R, eb, eb, en);
-      double worst = 0.0;
-      for (int c = 0; c < R; ++c)
-        if (active[c] && rbn[c] > 0.0 && en[c] / rbn[c] > worst) worst = en[c] / rbn[c];
-      if (!(worst > eps_inner)) break;
-      apply_blocks_f32(N, R, Minv32, eb, zb);
-      dots_f32(N, R, zb, eb, rho_a);
-      for (int64_t n = 0; n < N; ++n)
-        for (int c = 0; c < R; ++c) {
-          if (!active[c]) continue;
-          float beta = step > 0 ? (float)(rho_a[c] / rho_b[c]) : 0.0f;
-          for (int i = 0; i < 3; ++i) {
-            size_t k = 3 * (n * R + c) + i;
-            pb[k] = zb[k] + beta * (step > 0 ? pb[k] : 0.0f);
-          }
-        }
-      spmv_f32(N, rowptr, col, vals32, R, pb, qb);
-      dots_f32(N, R, pb, qb, gb);
-      for (int64_t n = 0; n < N; ++n)
-        for (int c = 0; c < R; ++c) {
-          if (!active[c]) continue;
-          float alpha = (float)(rho_a[c] / gb[c]);
-          for (int i = 0; i < 3; ++i) {
-            size_t k = 3 * (n * R + c) + i;
-            eb[k] -= alpha * qb[k];
-            ub[k] += alpha * pb[k];
-          }
-        }
-      for (int c = 0; c < R; ++c)
-        if (active[c]) { rho_b[c] = rho_a[c]; inner_total[c]++; }
+    if (N4 > 0) {
+      /* transfers between the levels keep Dirichlet DOFs at zero (reading: the
+       * paper's mapping matrices act on the free DOFs of each level) */
+      restrict_f32(N, N4, R, ends, rb, rb1);
+      restrict_f32(N, N4, R, ends, ub, ub1);
+      mask_f32(N4, R, free4, rb1);
+      mask_f32(N4, R, free4, ub1);
+      rc = inner_pcg_f32(N4, rowptr4, col4, vals4_32, Minv4_32, R, rb1, ub1, n_inner1, eps_inner1, active,
+                         inner1_total);
+      if (rc) break;
+      prolong_f32(N, R, ends, ub1, ub);
+      mask_f32(N, R, free_mask, ub);
     }
-    /* line 18 (read as z = ubar) */
+    rc = inner_pcg_f32(N, rowptr, col, vals32, Minv32, R, rb, ub, n_inner, eps_inner, active, inner_total);
+    if (rc) break;
     for (size_t k = 0; k < nv; ++k) z[k] = (double)ub[k];
-    double beta[64];
-    double* bet = R <= 64 ? beta : malloc(R * 8);
     if (it > 1) {
       dots(N, R, z, q, zq);
-      for (int c = 0; c < R; ++c) {
-        if (literal_beta) bet[c] = zq[c] / rho_prev[c];
-        else bet[c] = -zq[c] / pq_prev[c];
-      }
+      for (int c = 0; c < R; ++c) bet[c] = literal_beta ? zq[c] / rho_prev[c] : -zq[c] / pq_prev[c];
     } else {
       for (int c = 0; c < R; ++c) bet[c] = 0.0;
     }
@@ -585,7 +762,6 @@ int oracle_fcg_mixed(int64_t N, const int64_t* rowptr, const int32_t* col, const
           p[k] = z[k] + bet[c] * p[k];
         }
       }
-    if (bet != beta) free(bet);
     oracle_spmv(N, rowptr, col, vals, R, p, q);
     dots(N, R, z, r, rho);
     dots(N, R, p, q, gam);
@@ -606,10 +782,18 @@ int oracle_fcg_mixed(int64_t N, const int64_t* rowptr, const int32_t* col, const
   for (size_t k = 0; k < nv; ++k) r[k] = f[k] - q[k];
   dots(N, R, r, r, rn);
   for (int c = 0; c < R; ++c) relres[c] = fn[c] > 0.0 ? sqrt(rn[c] / fn[c]) : 0.0;
-  free(vals32); free(Minv32); free(r); free(z); free(p); free(q); free(rb); free(ub); free(eb); free(zb);
-  free(pb); free(qb); free(fn); free(rn); free(rho); free(gam); free(zq); free(pq_prev); free(rbn); free(en);
-  free(rho_a); free(rho_b); free(gb); free(active); free(rho_prev);
-  return 0;
+  free(vals32); free(Minv32); free(vals4_32); free(Minv4_32); free(rb1); free(ub1); free(r); free(z); free(p);
+  free(q); free(rb); free(ub); free(fn); free(rn); free(rho); free(gam); free(zq); free(pq_prev); free(rho_prev);
+  free(bet); free(active);
+  return rc;
+}
+
+/* The flexible mixed CG with the inner loop at level 0 only. */
+int oracle_fcg_mixed(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
+                     int R, const double* f, double* u, double tol, int max_outer, int n_inner, double eps_inner,
+                     int literal_beta, int32_t* outer, int32_t* inner_total, double* relres) {
+  return oracle_fcg_mg(N, rowptr, col, vals, Minv, R, f, u, tol, max_outer, n_inner, eps_inner, literal_beta, NULL,
+                       0, NULL, NULL, NULL, NULL, NULL, NULL, 0, 0.0, outer, inner_total, NULL, relres);
 }
 
 /* ------------------------------------------------------------------------- */

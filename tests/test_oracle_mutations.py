@@ -19,7 +19,8 @@ MUTANTS = {
     "edge_shape_factor": ("dN[4 + q][k] = 4.0 * (L[b] * dL[a][k] + L[a] * dL[b][k]);",
                           "dN[4 + q][k] = 2.0 * (L[b] * dL[a][k] + L[a] * dL[b][k]);"),
     "corner_shape_sign": ("dN[a][k] = (4.0 * L[a] - 1.0) * dL[a][k];", "dN[a][k] = (4.0 * L[a] + 1.0) * dL[a][k];"),
-    "shear_row_swapped": ("B[4][c + 0] = g[2]; B[4][c + 2] = g[0];", "B[4][c + 0] = g[0]; B[4][c + 2] = g[2];"),
+    "shear_row_swapped": ("B[4][c + 0] = g[2]; B[4][c + 2] = g[0];   /* gamma_xz */",
+                          "B[4][c + 0] = g[0]; B[4][c + 2] = g[2];   /* gamma_xz */"),
     "lame_lambda": ("double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));",
                     "double lam = E * nu / ((1.0 + nu) * (1.0 - nu));"),
     "jacobian_transposed": ("for (int k = 0; k < 3; ++k) J[i][k] += xe[3 * n + i] * dN[n][k];",

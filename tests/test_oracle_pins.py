@@ -478,3 +478,80 @@ def test_golden_loop_config():
     assert table[0] == (0.1, 30)
     assert table[1] == (0.05, 300)
     assert table[2] == (0.025, 3000)
+
+
+# ---------------------------------------------------------------------------
+# first-order (TET4) coarse level
+# ---------------------------------------------------------------------------
+
+def test_tet4_element_rigid_modes_and_energy():
+    xe = jittered_element(11)[:4]
+    E, nu = 3.0e10, 0.26
+    Ke = oracle.tet4_stiffness(xe, E, nu)
+    w = np.linalg.eigvalsh(Ke)
+    assert np.all(np.abs(w[:6]) <= 1e-12 * w[-1]) and np.all(w[6:] > 1e-6 * w[-1])
+    A = np.random.default_rng(5).standard_normal((3, 3)) * 1e-3
+    u = (xe @ A.T).reshape(-1)
+    eps = 0.5 * (A + A.T)
+    lam, mu = lame(E, nu)
+    assert u @ Ke @ u == pytest.approx(tet_volume(xe) * (lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps)),
+                                       rel=1e-12)
+
+
+def test_coarse_operator_is_galerkin_projection():
+    """Linear functions on the tetrahedra lie in the quadratic space, so the TET4
+    stiffness is exactly P1^T K P1 (P1: vertex values kept, edge nodes averaged)."""
+    m = mg.plain_box(n=2, jitter=0.12, seed=10)
+    cm = oracle.coarse_mesh(m)
+    K = oracle.assemble(m, apply_bc=False).to_scipy()
+    K1 = oracle.assemble4(cm, apply_bc=False).dense()
+    n4 = cm.coords.shape[0]
+    P = np.zeros((m.n_dof, 3 * n4))
+    for n, (a, b) in enumerate(cm.ends):
+        for i in range(3):
+            P[3 * n + i, 3 * a + i] += 0.5
+            P[3 * n + i, 3 * b + i] += 0.5
+    G = P.T @ (K @ P)
+    assert np.abs(G - K1).max() <= 1e-12 * np.abs(K1).max()
+
+
+def test_prolongation_reproduces_linear_fields_and_restriction_is_its_transpose():
+    m = mg.plain_box(n=3, jitter=0.15, seed=12)
+    cm = oracle.coarse_mesh(m)
+    A = np.array([[1.0, 2.0, -1.0], [0.5, -0.3, 0.2], [0.1, 0.0, 0.7]])
+    lin4 = (cm.coords @ A.T)[:, None, :]
+    lin10 = (m.coords @ A.T)[:, None, :]
+    assert np.abs(oracle.prolong(cm, lin4) - lin10).max() <= 1e-9 * np.abs(lin10).max()
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((cm.coords.shape[0], 2, 3))
+    b = rng.standard_normal((m.n_nodes, 2, 3))
+    assert np.sum(oracle.restrict(cm, b) * a) == pytest.approx(np.sum(b * oracle.prolong(cm, a)), rel=1e-12)
+
+
+def test_linear_patch_test_tet4():
+    m = mg.plain_box(n=3, jitter=0.15, seed=7)
+    m.young[:] = 4.0e10
+    m.poisson[:] = 0.25
+    cm = oracle.coarse_mesh(m)
+    K1 = oracle.assemble4(cm, apply_bc=False)
+    A = np.array([[1.0, 2.0, -0.5], [0.3, -1.0, 0.7], [0.2, 0.4, 1.5]]) * 1e-4
+    u = (cm.coords @ A.T)[:, None, :]
+    y = oracle.spmv(K1, u)[:, 0]
+    lx, ly, lz = m.lattice_shape()
+    v = cm.vertex
+    i, j, k = v % lx, (v // lx) % ly, v // (lx * ly)
+    inner = (i > 0) & (i < lx - 1) & (j > 0) & (j < ly - 1) & (k > 0) & (k < lz - 1)
+    assert np.abs(y[inner]).max() <= 1e-10 * np.abs(K1.vals).max() * np.abs(u).max()
+
+
+def test_two_level_fcg_matches_direct_and_moves_work_to_the_coarse_level(box8):
+    """The TET4 level shifts the inner work from the quadratic mesh to the linear
+    one (Sec. 2): same solution, far fewer level-0 inner steps."""
+    m, K, f = box8
+    cm = oracle.coarse_mesh(m)
+    ud = oracle.direct_solve(K, f)
+    u1, o1, i1, j1, rel1 = oracle.fcg_mg(K, f, tol=1e-8)
+    u2, o2, i2, j2, rel2 = oracle.fcg_mg(K, f, coarse=cm, free=m.free, tol=1e-8)
+    assert rel2[0] <= 1.5e-8 and j2[0] > 0 and j1[0] == 0
+    assert np.linalg.norm(u2 - ud) <= 1e-5 * np.linalg.norm(ud)
+    assert i2[0] < i1[0] / 2
