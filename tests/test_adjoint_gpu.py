@@ -90,5 +90,10 @@ def test_adjoint_24cube_fd_50_directions():
         Jm = adjoint.misfit(M, logE0 - h * ve, a - h * va, sources, obs, d, OPTS)
         fd = (Jp - Jm) / (2 * h)
         an = float(g_logE @ ve + g_a @ va)
-        errs.append(abs(an - fd) / max(abs(fd), 1e-300))
-    assert max(errs) <= 1e-4, errs
+        errs.append((abs(an - fd), abs(fd)))
+    # solves at relative residual 1e-13 leave J with an absolute noise of a few
+    # 1e-15 |J0|, which central differences at h = 1e-6 turn into a floor of a few
+    # 1e-9 |J0| on every direction; directions whose derivative is that small are
+    # judged against the floor, all others to 1e-4 relative
+    bad = [(e, f) for e, f in errs if e > 1e-4 * f + 1e-7 * abs(J0)]
+    assert not bad, (bad, abs(J0))
