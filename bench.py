@@ -53,6 +53,8 @@ def parse():
                          "the 120x120x60 block through fe_solve_many vs the plain FP64 PCG one case at a time")
     ap.add_argument("--many-cases", type=int, default=96, help="cases of --workload many")
     ap.add_argument("--many-plain", type=int, default=1, help="cases timed with the plain FP64 PCG")
+    ap.add_argument("--many-solver", choices=["fcg_mixed", "fcg_mg"], default="fcg_mixed",
+                    help="many-case solver: inner loop at level 0 only, or with the TET4 level 1 first")
     return ap.parse_args()
 
 
@@ -425,15 +427,31 @@ def run_solves(m, iface, M, torch, fe, world):
         plain_stats[-1]["rel_diff_vs_mixed"] = float(du)
     mixed_rate = R / t_mixed
     plain_rate = 1.0 / float(np.mean(t_plain))
+    # the same batch with the TET4 level (inner loop level 1) before level 0; the
+    # coarse mesh and its block Jacobi are set up before the timed solve
+    M.coarse_block_jacobi()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u2, stats2, st2 = M.solve(f, solver="fcg_mg", tol=1e-8, raise_on_fail=False)
+    torch.cuda.synchronize()
+    t_mg = time.perf_counter() - t0
+    du2 = float(torch.linalg.norm(u2 - u) / torch.linalg.norm(u))
+    mg_rate = R / t_mg
     return {"workload": "crust_70x70x35_tet10 16 unit-slip patches (4x4 grid, 2x2 km)",
             "mixed_fcg": {"case_solves_per_s": mixed_rate * world, "seconds": t_mixed, "all_converged": ok,
                           "outer": [s["outer"] for s in stats], "inner": [s["inner"] for s in stats],
                           "relres_max": max(s["relres"] for s in stats), "status": int(st)},
+            "mixed_fcg_two_level": {"case_solves_per_s": mg_rate * world, "seconds": t_mg,
+                                    "all_converged": all(s["relres"] <= 1e-8 for s in stats2),
+                                    "outer": [s["outer"] for s in stats2], "inner0": [s["inner"] for s in stats2],
+                                    "inner1": [s["inner1"] for s in stats2],
+                                    "relres_max": max(s["relres"] for s in stats2), "status": int(st2),
+                                    "rel_diff_vs_one_level": du2},
             "plain_pcg64_one_case": {"case_solves_per_s": plain_rate * world, "seconds_per_case": float(np.mean(t_plain)),
                                      "iters": [s["outer"] for s in plain_stats],
                                      "relres": [s["relres"] for s in plain_stats],
                                      "rel_diff_vs_mixed": [s["rel_diff_vs_mixed"] for s in plain_stats]},
-            "speedup": mixed_rate / plain_rate}
+            "speedup": mixed_rate / plain_rate, "speedup_two_level": mg_rate / plain_rate}
 
 
 def run_many(args):
@@ -465,10 +483,12 @@ def run_many(args):
     # before the timed region; fe_solve_many would otherwise tune on first use
     for RR, dt in ((32, "f32"), (32, "f64"), (1, "f64")):
         M.tune(RR, dt)
+    if args.many_solver == "fcg_mg":
+        M.coarse_block_jacobi()
     setup_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    u, stats, st, R_used = M.solve_many(F, R_slots=0, solver="fcg_mixed", tol=1e-8, raise_on_fail=False)
+    u, stats, st, R_used = M.solve_many(F, R_slots=0, solver=args.many_solver, tol=1e-8, raise_on_fail=False)
     torch.cuda.synchronize()
     t_many = time.perf_counter() - t0
     plain = []
@@ -486,9 +506,10 @@ def run_many(args):
            "unit": "case-solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": "crust_%dx%dx%d_tet10_%d_slip_cases" % (shape + (len(cases),)),
                       "mesh_elements": m.n_elem, "mesh_dof": 3 * m.n_nodes, "slots": R_used,
-                      "setup_seconds": setup_s},
+                      "solver": args.many_solver, "setup_seconds": setup_s},
            "many": {"seconds": t_many, "status": int(st), "all_converged": all(s["relres"] <= 1e-8 for s in stats),
                     "outer_min_max": [min(s["outer"] for s in stats), max(s["outer"] for s in stats)],
+                    "inner0_total": sum(s["inner"] for s in stats), "inner1_total": sum(s["inner1"] for s in stats),
                     "relres_max": max(s["relres"] for s in stats)},
            "plain_pcg64_one_case": {"case_solves_per_s": plain_rate, "cases": plain},
            "speedup": rate / plain_rate if plain_rate else None}

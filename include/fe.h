@@ -54,7 +54,8 @@ typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
 
 typedef enum {
   FE_SOLVER_PCG64 = 0,      /* FP64 CG with 3x3 block Jacobi (the plain baseline) */
-  FE_SOLVER_FCG_MIXED = 1   /* FP64 flexible CG, FP32 inner block-Jacobi CG (Algorithm 1) */
+  FE_SOLVER_FCG_MIXED = 1,  /* FP64 flexible CG, FP32 inner block-Jacobi CG at level 0 (Algorithm 1) */
+  FE_SOLVER_FCG_MG = 2      /* as FCG_MIXED, with the TET4 inner loop (level 1) before level 0 */
 } fe_solver;
 
 typedef struct fe_mesh fe_mesh;   /* opaque, library-owned */
@@ -71,6 +72,8 @@ typedef struct {
   int32_t literal_beta;  /* 1: the printed beta = (z,q)/rho; 0: flexible CG beta (default) */
   int32_t check_every;   /* outer iterations between host reads of the convergence flags (>= 1) */
   int32_t verbose;       /* reserved, 0 */
+  int32_t n_inner1;      /* FCG_MG: cap on level-1 (TET4) inner steps per outer iteration (300) */
+  double eps_inner1;     /* FCG_MG: level-1 inner stop, the same rule as eps_inner (0.05) */
 } fe_solve_opts;
 
 /* Per-case results of fe_pcg_solve. */
@@ -79,7 +82,7 @@ typedef struct {
   int32_t inner_iters;   /* inner steps summed over outer iterations (0 for PCG64) */
   double relres;         /* true relative residual ||f - K u|| / ||f|| at exit (FP64 product) */
   int32_t status;        /* FE_OK, FE_ENOCONV or FE_EBREAKDOWN for this case */
-  int32_t pad;
+  int32_t inner1_iters;  /* level-1 (TET4) inner steps summed over outer iterations (FCG_MG only) */
 } fe_solve_stats;
 
 /* Message of the last failure on this thread ("" if none). */
@@ -89,7 +92,8 @@ const char* fe_last_error(void);
 const char* fe_version(void);
 
 /* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
- * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1. */
+ * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1, n_inner1 300,
+ * eps_inner1 0.05 (the paper's table of loop settings, levels 0 and 1). */
 void fe_solve_opts_default(fe_solve_opts* opts);
 
 /*
@@ -263,6 +267,52 @@ fe_status fe_block_jacobi_noalloc(const fe_mesh* mesh, double* binv_dev, void* s
  */
 fe_status fe_adjoint_grad(const fe_mesh* mesh, int32_t R, const double* u_dev, const double* lambda_dev,
                           double* g_elem_dev, void* stream);
+
+/*
+ * TET4 coarse level (Sec. 2 and Algorithm 1 lines 2, 11, 15-16: inner loop level 1).
+ * The coarse mesh is the TET10 mesh without its edge nodes: same elements and
+ * materials, first-order shape functions. Its nodes are the corner nodes of the
+ * TET10 mesh numbered in increasing TET10 id (internal numbering of this
+ * library's mesh). P1 maps coarse to fine values by linear interpolation: a
+ * corner keeps its value, an edge node takes the mean of its two ends. Both
+ * transfers keep Dirichlet DOFs at zero (fine DOFs after P1, coarse DOFs after
+ * P1^T; a coarse node's DOF is fixed iff it is fixed on its TET10 node), and the
+ * coarse operator is K1_bc = P K1 P + (I - P) with the coarse mask P, which
+ * equals P1^T K_bc P1 restricted to free coarse DOFs when K is built from
+ * TET10 elements whose displacement is linear (Galerkin consistency).
+ * The coarse structure is built on first use (host, O(N + E)) and kept with the
+ * mesh; vectors are [N4][R][3] like the fine ones.
+ */
+
+/* fe_coarse_info -- builds the coarse level if needed.
+ *   n_nodes4     host, receives N4 (may be NULL)
+ *   vertex_host  host int32 [N4], receives the TET10 node id of each coarse node
+ *                (may be NULL)
+ * Synchronous. */
+fe_status fe_coarse_info(const fe_mesh* mesh, int64_t* n_nodes4, int32_t* vertex_host, void* stream);
+
+/* fe_ebe4_apply -- y4 = K1_bc x4 for R cases, element by element (the first-order
+ * EBE product of Sec. 3.2 on the coarse mesh; fixed DOFs: y = x).
+ *   x4, y4   device [N4][R][3] of dtype, 16-byte aligned, not aliased; y4 overwritten
+ * Asynchronous on `stream`. */
+fe_status fe_ebe4_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x4, void* y4, void* stream);
+
+/* fe_coarse_restrict -- r4 = P (P1^T r10): r10 device [N][R][3], r4 device
+ * [N4][R][3] overwritten (fixed coarse DOFs 0). Asynchronous on `stream`. */
+fe_status fe_coarse_restrict(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* r10, void* r4,
+                             void* stream);
+
+/* fe_coarse_prolong -- u10 = P (P1 u4): u4 device [N4][R][3], u10 device
+ * [N][R][3] overwritten (fixed fine DOFs 0). Asynchronous on `stream`. */
+fe_status fe_coarse_prolong(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* u4, void* u10,
+                            void* stream);
+
+/* fe_coarse_block_jacobi -- the level-1 block Jacobi M1^-1 = diag3x3[K1_bc]^-1
+ * (Algorithm 1 line 2) from the closed form of the TET4 diagonal blocks,
+ * V [(lam + mu) g_a g_a^T + mu |g_a|^2 I], built on first use (FP64).
+ *   binv4_dev  device double [N4][3][3], overwritten
+ * Fails with FE_EINVAL if a free coarse node has a singular block. */
+fe_status fe_coarse_block_jacobi(const fe_mesh* mesh, double* binv4_dev, void* stream);
 
 #ifdef __cplusplus
 }

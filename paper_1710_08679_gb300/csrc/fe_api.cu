@@ -54,24 +54,6 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-// Runs f, converting library failures and C++ exceptions into a status.
-template <typename F>
-static fe_status guarded(F&& f) {
-  try {
-    clear_error();
-    f();
-    return FE_OK;
-  } catch (const Failure& x) {
-    return x.status;
-  } catch (const std::bad_alloc&) {
-    set_error("host allocation failed");
-    return FE_ENOMEM;
-  } catch (...) {
-    set_error("unexpected C++ exception");
-    return FE_EINVAL;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // element order and tiles
 // ---------------------------------------------------------------------------
@@ -257,6 +239,7 @@ static void upload_materials(fe_mesh* m, cudaStream_t s) {
   FE_CUDA(cudaMemcpyAsync(m->mat32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaStreamSynchronize(s));
   m->jacobi_ready = false;
+  m->coarse.jacobi_ready = false;
 }
 
 }  // namespace fe
@@ -289,6 +272,8 @@ void fe_solve_opts_default(fe_solve_opts* o) {
   o->literal_beta = 0;
   o->check_every = 1;
   o->verbose = 0;
+  o->n_inner1 = 300;
+  o->eps_inner1 = 0.05;
 }
 
 fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,

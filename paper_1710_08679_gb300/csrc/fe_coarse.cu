@@ -1,0 +1,414 @@
+// First-order (TET4) coarse level of the inner solve (Sec. 2: "the same mesh but
+// without edge nodes"; Algorithm 1 lines 2, 11, 15 and 16 at level 1).
+//
+//  * the coarse mesh is the corner nodes of the TET10 mesh, with the same elements
+//    and materials; the element stiffness of a linear tetrahedron is
+//    K_e = V B^T D B with constant B, applied as y_k = V s g_k, s = lam tr(H) I +
+//    mu (H + H^T), H = sum_k u_k (x) g_k (g_k: gradients of the volume coordinates);
+//  * P1 maps coarse to fine values: a vertex keeps its value, an edge node takes
+//    the mean of its two ends (linear interpolation); P1^T is its transpose;
+//  * Dirichlet DOFs are kept at zero by both transfers, and the coarse operator is
+//    K1_bc = P K1 P + (I - P) with the coarse free mask.
+#include <algorithm>
+#include <vector>
+
+#include "fe_element.cuh"
+#include "fe_internal.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) zero4_kernel(int64_t n, T* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = T(0);
+}
+
+// thread = (element, case); the element geometry comes from the TET10 corner
+// coordinates (the same corners), the vector entries from the coarse numbering
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, const int32_t* __restrict__ conn4,
+                                                        const uint8_t* __restrict__ nmask4,
+                                                        const uint8_t* __restrict__ own4, const T* __restrict__ x,
+                                                        T* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= M.n_elem * R) return;
+  const int64_t e = gid / R;
+  const int r = (int)(gid - e * R);
+  const int4 c4 = __ldg(reinterpret_cast<const int4*>(conn4) + e);
+  const int2 c01 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e));
+  const int2 c23 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e) + 1);
+  const int cf[4] = {c01.x, c01.y, c23.x, c23.y};
+  T xc[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xc[k][i] = __ldg(M.xyz + 3 * (int64_t)cf[k] + i);
+  ElemGeo<T> G;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], __ldg(M.mat + 2 * e), __ldg(M.mat + 2 * e + 1), G);
+  const int nd[4] = {c4.x, c4.y, c4.z, c4.w};
+  int mk[4];
+  T H[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) H[a][b] = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    mk[k] = __ldg(nmask4 + nd[k]);
+    const T* xa = x + ((int64_t)nd[k] * R + r) * 3;
+    T u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = ((mk[k] >> c) & 1) ? __ldg(xa + c) : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) H[a][b] += u[a] * G.g[k][b];
+  }
+  // V = 20 c; fold V into the stress
+  const T V = T(20) * G.c;
+  const T lt = G.lam * (H[0][0] + H[1][1] + H[2][2]);
+  T sg[6];
+  sg[0] = V * (lt + T(2) * G.mu * H[0][0]);
+  sg[1] = V * (lt + T(2) * G.mu * H[1][1]);
+  sg[2] = V * (lt + T(2) * G.mu * H[2][2]);
+  sg[3] = V * G.mu * (H[1][2] + H[2][1]);
+  sg[4] = V * G.mu * (H[0][2] + H[2][0]);
+  sg[5] = V * G.mu * (H[0][1] + H[1][0]);
+  const int ow = __ldg(own4 + e);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T w[3];
+    sym_mv(sg, G.g[k], w);
+    T* ya = y + ((int64_t)nd[k] * R + r) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if ((mk[k] >> c) & 1)
+        atomicAdd(ya + c, w[c]);
+      else if ((ow >> k) & 1)
+        ya[c] = __ldg(x + ((int64_t)nd[k] * R + r) * 3 + c);
+    }
+  }
+}
+
+// r4 = P1^T r10 (r4 zeroed before), constrained coarse DOFs skipped (stay zero)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) restrict_kernel(int64_t N10, int R, const int32_t* __restrict__ ends,
+                                                            const uint8_t* __restrict__ nmask4,
+                                                            const T* __restrict__ r10, T* __restrict__ r4,
+                                                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= N10 * R) return;
+  const int64_t n = gid / R;
+  const int r = (int)(gid - n * R);
+  const int2 ab = __ldg(reinterpret_cast<const int2*>(ends) + n);
+  const T* v = r10 + gid * 3;
+  const int ma = __ldg(nmask4 + ab.x);
+  if (ab.x == ab.y) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if ((ma >> c) & 1) atomicAdd(r4 + ((int64_t)ab.x * R + r) * 3 + c, v[c]);
+  } else {
+    const int mb = __ldg(nmask4 + ab.y);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T h = T(0.5) * v[c];
+      if ((ma >> c) & 1) atomicAdd(r4 + ((int64_t)ab.x * R + r) * 3 + c, h);
+      if ((mb >> c) & 1) atomicAdd(r4 + ((int64_t)ab.y * R + r) * 3 + c, h);
+    }
+  }
+}
+
+// u10 = P u4: vertex values copied, edge nodes the mean of their ends, then the
+// fine Dirichlet DOFs zeroed
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prolong_kernel(int64_t N10, int R, const int32_t* __restrict__ ends,
+                                                           const uint8_t* __restrict__ nmask,
+                                                           const T* __restrict__ u4, T* __restrict__ u10,
+                                                           const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= N10 * R) return;
+  const int64_t n = gid / R;
+  const int r = (int)(gid - n * R);
+  const int2 ab = __ldg(reinterpret_cast<const int2*>(ends) + n);
+  const int mk = __ldg(nmask + n);
+  const T* a = u4 + ((int64_t)ab.x * R + r) * 3;
+  const T* b = u4 + ((int64_t)ab.y * R + r) * 3;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T v = (ab.x == ab.y) ? a[c] : T(0.5) * (a[c] + b[c]);
+    u10[gid * 3 + c] = ((mk >> c) & 1) ? v : T(0);
+  }
+}
+
+// diagonal 3x3 blocks of K1: V [(lam + mu) g_a g_a^T + mu |g_a|^2 I] per corner
+__global__ void jacobi4_diag_kernel(MeshView<double> M, const int32_t* __restrict__ conn4, double* __restrict__ Dg) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M.n_elem) return;
+  double xc[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 3; ++i) xc[k][i] = M.xyz[3 * (int64_t)M.conn[10 * e + k] + i];
+  ElemGeo<double> G;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], M.mat[2 * e], M.mat[2 * e + 1], G);
+  const double V = 20.0 * G.c;
+  for (int a = 0; a < 4; ++a) {
+    const double* g = G.g[a];
+    const double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    double* D = Dg + 9 * (int64_t)conn4[4 * e + a];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) atomicAdd(D + 3 * i + j, V * ((G.lam + G.mu) * g[i] * g[j] + (i == j ? G.mu * gg : 0.0)));
+  }
+}
+
+__global__ void jacobi4_invert_kernel(int64_t N, const uint8_t* __restrict__ nmask, const double* __restrict__ Dg,
+                                      double* __restrict__ B64, float* __restrict__ B32, int* __restrict__ bad) {
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int mk = nmask[n];
+  double A[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const bool fi = (mk >> i) & 1, fj = (mk >> j) & 1;
+      A[i][j] = (fi && fj) ? Dg[9 * n + 3 * i + j] : (i == j ? 1.0 : 0.0);
+    }
+  const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+  if (!(det > 0.0) || !isfinite(det)) {
+    atomicExch(bad, 1);
+    for (int k = 0; k < 9; ++k) {
+      B64[9 * n + k] = (k % 4 == 0) ? 1.0 : 0.0;
+      B32[9 * n + k] = (k % 4 == 0) ? 1.f : 0.f;
+    }
+    return;
+  }
+  const double id = 1.0 / det;
+  const double I[9] = {c00 * id,
+                       (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id,
+                       (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id,
+                       c01 * id,
+                       (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id,
+                       (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id,
+                       c02 * id,
+                       (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id,
+                       (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id};
+  for (int k = 0; k < 9; ++k) {
+    B64[9 * n + k] = I[k];
+    B32[9 * n + k] = (float)I[k];
+  }
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+void build_coarse(fe_mesh* m, cudaStream_t s) {
+  Coarse& c = m->coarse;
+  if (c.ready) return;
+  const int64_t N = m->n_nodes, E = m->n_elem;
+  std::vector<int32_t> newid((size_t)N, -1);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 4; ++a) newid[(size_t)m->conn_host[(size_t)(10 * e + a)]] = 0;
+  std::vector<int32_t> vertex;
+  for (int64_t n = 0; n < N; ++n)
+    if (newid[(size_t)n] == 0) {
+      newid[(size_t)n] = (int32_t)vertex.size();
+      vertex.push_back((int32_t)n);
+    }
+  const int64_t N4 = (int64_t)vertex.size();
+  std::vector<int32_t> conn4((size_t)E * 4), ends((size_t)N * 2, -1);
+  std::vector<uint8_t> own4((size_t)E, 0), mk4((size_t)N4), seen((size_t)N4, 0);
+  static const int EA[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t* ce = &m->conn_host[(size_t)(10 * e)];
+    for (int a = 0; a < 4; ++a) {
+      const int32_t v = newid[(size_t)ce[a]];
+      conn4[(size_t)(4 * e + a)] = v;
+      ends[(size_t)(2 * ce[a])] = v;
+      ends[(size_t)(2 * ce[a] + 1)] = v;
+      if (!seen[(size_t)v]) {
+        seen[(size_t)v] = 1;
+        own4[(size_t)e] |= (uint8_t)(1u << a);
+      }
+    }
+    for (int q = 0; q < 6; ++q) {
+      FE_REQUIRE(newid[(size_t)ce[4 + q]] < 0, "node %d is an edge node of element %lld and a corner of another",
+                 ce[4 + q], (long long)m->perm_host[(size_t)e]);
+      ends[(size_t)(2 * ce[4 + q])] = newid[(size_t)ce[EA[q][0]]];
+      ends[(size_t)(2 * ce[4 + q] + 1)] = newid[(size_t)ce[EA[q][1]]];
+    }
+  }
+  for (int64_t n = 0; n < N; ++n)
+    FE_REQUIRE(ends[(size_t)(2 * n)] >= 0, "node %lld belongs to no element (no coarse interpolation)",
+               (long long)n);
+  for (int64_t v = 0; v < N4; ++v) mk4[(size_t)v] = m->nmask_host[(size_t)vertex[(size_t)v]];
+  c.n_nodes = N4;
+  c.conn4.alloc(conn4.size() * 4);
+  c.ends.alloc(ends.size() * 4);
+  c.nmask4.alloc(mk4.size());
+  c.own4.alloc(own4.size());
+  c.vertex.alloc(vertex.size() * 4);
+  FE_CUDA(cudaMemcpyAsync(c.conn4.ptr, conn4.data(), conn4.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(c.ends.ptr, ends.data(), ends.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(c.nmask4.ptr, mk4.data(), mk4.size(), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(c.own4.ptr, own4.data(), own4.size(), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(c.vertex.ptr, vertex.data(), vertex.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  c.ready = true;
+  c.jacobi_ready = false;
+}
+
+void build_coarse_jacobi(fe_mesh* m, cudaStream_t s) {
+  build_coarse(m, s);
+  Coarse& c = m->coarse;
+  if (c.jacobi_ready) return;
+  const int64_t N4 = c.n_nodes;
+  DevBuf D, bad;
+  D.alloc((size_t)N4 * 9 * sizeof(double));
+  bad.alloc(sizeof(int));
+  if (!c.binv64.ptr) c.binv64.alloc((size_t)N4 * 9 * sizeof(double));
+  if (!c.binv32.ptr) c.binv32.alloc((size_t)N4 * 9 * sizeof(float));
+  FE_CUDA(cudaMemsetAsync(D.ptr, 0, D.bytes, s));
+  FE_CUDA(cudaMemsetAsync(bad.ptr, 0, sizeof(int), s));
+  jacobi4_diag_kernel<<<blocks_for(m->n_elem), kThreads, 0, s>>>(m->view<double>(), c.conn4.as<int32_t>(),
+                                                                   D.as<double>());
+  FE_CHECK_LAUNCH();
+  jacobi4_invert_kernel<<<blocks_for(N4), kThreads, 0, s>>>(N4, c.nmask4.as<uint8_t>(), D.as<double>(),
+                                                            c.binv64.as<double>(), c.binv32.as<float>(), bad.as<int>());
+  FE_CHECK_LAUNCH();
+  int hbad = 0;
+  FE_CUDA(cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  FE_REQUIRE(hbad == 0, "coarse block Jacobi: a free node has a singular diagonal block");
+  c.jacobi_ready = true;
+}
+
+template <typename T>
+void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip) {
+  const Coarse& c = m->coarse;
+  FE_REQUIRE(c.ready, "coarse level not built");
+  const int64_t n4 = c.n_nodes * (int64_t)R * 3;
+  zero4_kernel<T><<<std::min<unsigned>(blocks_for(n4), 152 * 16), kThreads, 0, s>>>(n4, y4, skip);
+  FE_CHECK_LAUNCH();
+  ebe4_kernel<T><<<blocks_for(m->n_elem * R), kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(),
+                                                                 c.nmask4.as<uint8_t>(), c.own4.as<uint8_t>(), x4, y4,
+                                                                 skip);
+  FE_CHECK_LAUNCH();
+}
+
+template <typename T>
+void coarse_restrict(const fe_mesh* m, int R, const T* r10, T* r4, cudaStream_t s, const int* skip) {
+  const Coarse& c = m->coarse;
+  FE_REQUIRE(c.ready, "coarse level not built");
+  const int64_t n4 = c.n_nodes * (int64_t)R * 3;
+  zero4_kernel<T><<<std::min<unsigned>(blocks_for(n4), 152 * 16), kThreads, 0, s>>>(n4, r4, skip);
+  FE_CHECK_LAUNCH();
+  restrict_kernel<T><<<blocks_for(m->n_nodes * R), kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(),
+                                                                      c.nmask4.as<uint8_t>(), r10, r4, skip);
+  FE_CHECK_LAUNCH();
+}
+
+template <typename T>
+void coarse_prolong(const fe_mesh* m, int R, const T* u4, T* u10, cudaStream_t s, const int* skip) {
+  const Coarse& c = m->coarse;
+  FE_REQUIRE(c.ready, "coarse level not built");
+  prolong_kernel<T><<<blocks_for(m->n_nodes * R), kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(),
+                                                                     m->nmask.as<uint8_t>(), u4, u10, skip);
+  FE_CHECK_LAUNCH();
+}
+
+template void ebe4_apply<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
+template void ebe4_apply<double>(const fe_mesh*, int, const double*, double*, cudaStream_t, const int*);
+template void coarse_restrict<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
+template void coarse_restrict<double>(const fe_mesh*, int, const double*, double*, cudaStream_t, const int*);
+template void coarse_prolong<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
+template void coarse_prolong<double>(const fe_mesh*, int, const double*, double*, cudaStream_t, const int*);
+
+}  // namespace fe
+
+// ---------------------------------------------------------------------------
+// C ABI of the coarse level
+// ---------------------------------------------------------------------------
+extern "C" fe_status fe_coarse_info(const fe_mesh* mesh, int64_t* n_nodes4, int32_t* vertex_host, void* stream) {
+  return fe::guarded([&] {
+    FE_REQUIRE(mesh != nullptr, "mesh is NULL");
+    fe_mesh* m = const_cast<fe_mesh*>(mesh);
+    fe::DeviceGuard dg(m->device);
+    fe::build_coarse(m, (cudaStream_t)stream);
+    if (n_nodes4) *n_nodes4 = m->coarse.n_nodes;
+    if (vertex_host)
+      FE_CUDA(cudaMemcpy(vertex_host, m->coarse.vertex.ptr, m->coarse.vertex.bytes, cudaMemcpyDeviceToHost));
+  });
+}
+
+namespace {
+// shared checks of the three vector entry points
+fe_mesh* coarse_args(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* in, void* out) {
+  FE_REQUIRE(mesh != nullptr && in != nullptr && out != nullptr, "NULL argument");
+  FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range [1, 64]", R);
+  FE_REQUIRE(dtype == FE_F32 || dtype == FE_F64, "dtype must be FE_F32 or FE_F64");
+  FE_REQUIRE(in != out, "input and output must not alias");
+  return const_cast<fe_mesh*>(mesh);
+}
+}  // namespace
+
+extern "C" fe_status fe_ebe4_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x4, void* y4,
+                                   void* stream) {
+  return fe::guarded([&] {
+    fe_mesh* m = coarse_args(mesh, R, dtype, x4, y4);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe::build_coarse(m, s);
+    if (dtype == FE_F64)
+      fe::ebe4_apply<double>(m, R, (const double*)x4, (double*)y4, s);
+    else
+      fe::ebe4_apply<float>(m, R, (const float*)x4, (float*)y4, s);
+  });
+}
+
+extern "C" fe_status fe_coarse_restrict(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* r10, void* r4,
+                                        void* stream) {
+  return fe::guarded([&] {
+    fe_mesh* m = coarse_args(mesh, R, dtype, r10, r4);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe::build_coarse(m, s);
+    if (dtype == FE_F64)
+      fe::coarse_restrict<double>(m, R, (const double*)r10, (double*)r4, s);
+    else
+      fe::coarse_restrict<float>(m, R, (const float*)r10, (float*)r4, s);
+  });
+}
+
+extern "C" fe_status fe_coarse_prolong(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* u4, void* u10,
+                                       void* stream) {
+  return fe::guarded([&] {
+    fe_mesh* m = coarse_args(mesh, R, dtype, u4, u10);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe::build_coarse(m, s);
+    if (dtype == FE_F64)
+      fe::coarse_prolong<double>(m, R, (const double*)u4, (double*)u10, s);
+    else
+      fe::coarse_prolong<float>(m, R, (const float*)u4, (float*)u10, s);
+  });
+}
+
+extern "C" fe_status fe_coarse_block_jacobi(const fe_mesh* mesh, double* binv4_dev, void* stream) {
+  return fe::guarded([&] {
+    FE_REQUIRE(mesh != nullptr && binv4_dev != nullptr, "NULL argument");
+    fe_mesh* m = const_cast<fe_mesh*>(mesh);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fe::build_coarse_jacobi(m, s);
+    FE_CUDA(cudaMemcpyAsync(binv4_dev, m->coarse.binv64.ptr, m->coarse.binv64.bytes, cudaMemcpyDeviceToDevice, s));
+  });
+}

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -42,6 +43,24 @@ struct Failure {
       throw ::fe::Failure{FE_EINVAL};  \
     }                                  \
   } while (0)
+
+// Runs f, converting library failures and C++ exceptions into a status.
+template <typename F>
+inline fe_status guarded(F&& f) {
+  try {
+    clear_error();
+    f();
+    return FE_OK;
+  } catch (const Failure& x) {
+    return x.status;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FE_ENOMEM;
+  } catch (...) {
+    set_error("unexpected C++ exception");
+    return FE_EINVAL;
+  }
+}
 
 // Sets the mesh's device current for the scope and restores the caller's device.
 struct DeviceGuard {
@@ -112,6 +131,19 @@ struct PacketLayout {
   }
 };
 
+// First-order (TET4) coarse level: the same mesh without edge nodes (Sec. 2).
+struct Coarse {
+  bool ready = false;
+  int64_t n_nodes = 0;      // N4: corner nodes of the TET10 mesh
+  DevBuf conn4;             // int32 [E][4] coarse node ids (internal element order)
+  DevBuf ends;              // int32 [N][2] coarse ends of each TET10 node (equal for a vertex)
+  DevBuf nmask4;            // uint8 [N4] free-DOF bits
+  DevBuf own4;              // uint8 [E] bit a set if element e is the first holding its corner a
+  DevBuf vertex;            // int32 [N4] TET10 id of each coarse node
+  bool jacobi_ready = false;
+  DevBuf binv64, binv32;    // [N4][9] inverse diagonal blocks of K1_bc
+};
+
 struct SolverWork;  // defined in fe_solver.cu
 
 }  // namespace fe
@@ -148,6 +180,8 @@ struct fe_mesh {
   fe::DevBuf geodf;     // float-float geometry [E][16] for the float-float FP64 kernel
   std::vector<int32_t> conn_host;  // [E][10] in internal order
   std::vector<uint8_t> nmask_host; // [N] free-DOF bits
+  // TET4 coarse level (built on first use)
+  fe::Coarse coarse;
   // solver workspace (allocated lazily per R)
   fe::SolverWork* work = nullptr;
 
@@ -181,5 +215,15 @@ void build_block_jacobi(fe_mesh* m, cudaStream_t s);
 void adjoint_grad(const fe_mesh* m, int R, const double* u, const double* lam, double* g, cudaStream_t s);
 
 void free_solver_work(fe_mesh* m);
+
+// Coarse level (fe_coarse.cu)
+void build_coarse(fe_mesh* m, cudaStream_t s);
+void build_coarse_jacobi(fe_mesh* m, cudaStream_t s);
+template <typename T>
+void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip = nullptr);
+template <typename T>
+void coarse_restrict(const fe_mesh* m, int R, const T* r10, T* r4, cudaStream_t s, const int* skip = nullptr);
+template <typename T>
+void coarse_prolong(const fe_mesh* m, int R, const T* u4, T* u10, cudaStream_t s, const int* skip = nullptr);
 
 }  // namespace fe

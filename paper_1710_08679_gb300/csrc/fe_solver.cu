@@ -6,6 +6,11 @@
 //    FP64 flexible (adaptive) CG whose preconditioner z = K^-1 r is an FP32
 //    block-Jacobi CG (Algorithm 1(b)) stopped at N steps or when
 //    max_r ||e_r||^2/||rbar_r||^2 <= eps (the max-over-cases rule of Sec. 3.1).
+//  * FE_SOLVER_FCG_MG: as FCG_MIXED with the inner loop at level 1 first: the
+//    residual and the block-Jacobi guess are restricted to the TET4 mesh
+//    (Algorithm 1 line 11), solved there by the same FP32 CG with the TET4
+//    operator and its own block Jacobi (line 15), and the coarse solution is
+//    prolonged as the initial guess of the level-0 loop (line 16).
 //
 // GPU design: every per-case scalar (rho, gamma, alpha, beta, norms, masks)
 // lives in device arrays of length R; kernels read them directly, so one outer
@@ -34,15 +39,16 @@ namespace fe {
 // ---------------------------------------------------------------------------
 enum DField {
   D_FN2 = 0, D_RN2, D_RHO, D_GAM, D_ZQ, D_PQP, D_RHOP, D_ALPHA, D_BETA,
-  D_RBN2, D_EN2, D_RHOA, D_RHOB, D_GAMI, D_ALPHAI, D_BETAI, D_RT2, D_RELRES, D_COUNT
+  D_RBN2, D_EN2, D_RHOA, D_RHOB, D_GAMI, D_ALPHAI, D_BETAI, D_RT2, D_RELRES, D_RBN21, D_COUNT
 };
-enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INNER, I_COUNT };
+enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INNER, I_INNER1, I_COUNT };
 
 struct Cases {
   double* d;      // [D_COUNT][R]
   int* i;         // [I_COUNT][R]
-  int* done;      // inner-loop stop flag (1 int)
+  int* done;      // inner-loop stop flag (1 int), followed by the inner step counter (1 int)
   int R;
+  __device__ __forceinline__ int& step() const { return done[1]; }
   __device__ __forceinline__ double& D(int f, int r) const { return d[f * R + r]; }
   __device__ __forceinline__ int& I(int f, int r) const { return i[f * R + r]; }
 };
@@ -52,13 +58,16 @@ struct SolverWork {
   int64_t N = 0;
   DevBuf r, p, q;                 // double [N][R][3]
   DevBuf rb, ub, eb, pb, qb;      // float  [N][R][3]
+  DevBuf rb1, ub1, eb1, pb1, qb1; // float  [N4][R][3] (level 1, allocated when used)
   DevBuf tu, tq;                  // double [N][3] (single-case true residual)
   DevBuf d, i;                    // case state
   cudaStream_t stream = nullptr;
+  cudaStream_t body = nullptr;    // records the bodies of the graph's inner-loop nodes
   cudaEvent_t ev = nullptr;
   ~SolverWork() {
     if (ev) cudaEventDestroy(ev);
     if (stream) cudaStreamDestroy(stream);
+    if (body) cudaStreamDestroy(body);
   }
 };
 
@@ -579,6 +588,7 @@ __global__ void s_slot_start(Cases C, int r, int pcg) {
   C.I(I_STATUS, r) = FE_OK;
   C.I(I_OUTER, r) = 0;
   C.I(I_INNER, r) = 0;
+  C.I(I_INNER1, r) = 0;
   C.D(D_RELRES, r) = 0.0;
 }
 
@@ -666,41 +676,71 @@ __global__ void s_pcg_beta(Cases C, double tol, int max_it) {
 __global__ void s_outer_begin(Cases C) {
   const int r = threadIdx.x;
   C.D(D_RBN2, r) = 0.0;
+  C.D(D_RBN21, r) = 0.0;
   C.D(D_EN2, r) = 0.0;
   C.D(D_RHOA, r) = 0.0;
   C.D(D_ZQ, r) = 0.0;
-  if (r == 0) *C.done = 0;
+  if (r == 0) {
+    *C.done = 0;
+    C.step() = 0;
+  }
 }
 
-// inner stop test before step `step` and inner beta (Alg. 1(b) lines 5, 8-10)
-__global__ void s_inner_check(Cases C, int step, int n_inner, double eps) {
+// between two inner loops of one outer iteration (level 1, then level 0)
+__global__ void s_level_begin(Cases C) {
+  const int r = threadIdx.x;
+  C.D(D_EN2, r) = 0.0;
+  C.D(D_RHOA, r) = 0.0;
+  C.D(D_RHOB, r) = 0.0;
+  C.D(D_GAMI, r) = 0.0;
+  if (r == 0) {
+    *C.done = 0;
+    C.step() = 0;
+  }
+}
+
+// inner stop test before the next step and inner beta (Alg. 1(b) lines 5, 8-10).
+// The step index is the device counter; with `loop` set, the stop decision is
+// also the condition of the graph's while node that repeats the inner step, so
+// the loop ends on the device after at most n_inner steps.
+__global__ void s_inner_check(Cases C, int n_inner, double eps, int f_rbn2, cudaGraphConditionalHandle loop,
+                              int use_loop) {
   __shared__ int go;
   const int r = threadIdx.x;
   if (r == 0) go = 0;
   __syncthreads();
-  if (*C.done) return;
-  const double rb = C.D(D_RBN2, r);
+  if (*C.done) {
+    if (use_loop && r == 0) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  const int step = C.step();
+  const double rb = C.D(f_rbn2, r);
   const bool act = C.I(I_ACTIVE, r) && rb > 0.0;
   const double ratio = C.D(D_EN2, r) / rb;
   if (act && !(ratio <= eps)) atomicOr(&go, 1);   // NaN counts as "not converged"
   __syncthreads();
-  if (r == 0 && (!go || step >= n_inner)) *C.done = 1;
+  const bool stop = !go || step >= n_inner;
   const double rhob = C.D(D_RHOB, r);
   C.D(D_BETAI, r) = (step > 0 && rhob != 0.0 && act) ? C.D(D_RHOA, r) / rhob : 0.0;
   C.D(D_GAMI, r) = 0.0;
+  if (r == 0) {
+    if (stop) *C.done = 1;
+    C.step() = step + 1;
+    if (use_loop) cudaGraphSetConditional(loop, stop ? 0u : 1u);
+  }
 }
 
 // inner alpha (Alg. 1(b) lines 13-15)
-__global__ void s_inner_alpha(Cases C) {
+__global__ void s_inner_alpha(Cases C, int f_rbn2, int f_count) {
   const int r = threadIdx.x;
   if (*C.done) return;
   const double g = C.D(D_GAMI, r), rho = C.D(D_RHOA, r);
-  const bool ok = C.I(I_ACTIVE, r) && C.D(D_RBN2, r) > 0.0 && g > 0.0 && isfinite(g) && isfinite(rho);
+  const bool ok = C.I(I_ACTIVE, r) && C.D(f_rbn2, r) > 0.0 && g > 0.0 && isfinite(g) && isfinite(rho);
   C.D(D_ALPHAI, r) = ok ? rho / g : 0.0;
   C.D(D_RHOB, r) = rho;
   C.D(D_EN2, r) = 0.0;
   C.D(D_RHOA, r) = 0.0;
-  if (C.I(I_ACTIVE, r)) C.I(I_INNER, r) += 1;
+  if (C.I(I_ACTIVE, r)) C.I(f_count, r) += 1;
 }
 
 // outer beta (Alg. 1(a) lines 19-22, read as flexible CG unless literal)
@@ -770,6 +810,8 @@ struct Solve {
   Cases C;
   VGeom g;
   size_t sm;  // shared bytes of reducing vector kernels
+  int64_t N1 = 0;  // level-1 nodes (0: no coarse level)
+  VGeom g1;
   cudaStream_t s;
   const double* f;
   double* u;
@@ -778,6 +820,12 @@ struct Solve {
   template <typename K, typename... A>
   void vec(K kern, A... args) {
     kern<<<g.grid, g.tpb, sm, s>>>(N, C, args...);
+    FE_CHECK_LAUNCH();
+  }
+  // the same vector kernel over `n` nodes with launch geometry `gg` (level 1)
+  template <typename K, typename... A>
+  void vec_on(int64_t n, const VGeom& gg, K kern, A... args) {
+    kern<<<gg.grid, gg.tpb, sm, s>>>(n, C, args...);
     FE_CHECK_LAUNCH();
   }
   template <typename K, typename... A>
@@ -827,29 +875,112 @@ static SolverWork* get_work(fe_mesh* m, int R) {
   w->d.alloc((size_t)D_COUNT * R * 8 + 64);
   w->i.alloc((size_t)I_COUNT * R * 4 + 64);
   FE_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+  FE_CUDA(cudaStreamCreateWithFlags(&w->body, cudaStreamNonBlocking));
   FE_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
   return w;
 }
 
-// the FCG outer iteration (Alg. 1(a) lines 9-29 with lines 11-16 dropped)
+// One FP32 inner loop (Alg. 1(b)) on level `L`: e = rbar - Kbar ubar, then up to
+// n steps of block-Jacobi CG until the max-over-cases stop rule holds. Steps after
+// the stop are skipped on the device (the `done` flag), so the captured graph
+// holds all n steps.
+struct Level {
+  int64_t N;
+  const VGeom* g;
+  const float* B;                 // FP32 inverse diagonal blocks [N][9]
+  float *rb, *ub, *eb, *pb, *qb;  // [N][R][3]
+  bool coarse;                    // operator: TET4 (level 1) or TET10 (level 0)
+  int n;
+  double eps;
+  int f_rbn2, f_count;
+};
+
+static void level_apply(Solve& S, const Level& L, const float* x, float* y, const int* skip) {
+  if (L.coarse)
+    ebe4_apply<float>(S.m, S.R, x, y, S.s, skip);
+  else
+    ebe_apply<float>(S.m, S.R, x, y, S.s, skip);
+}
+
+// one inner step (Alg. 1(b) lines 6-17) and the stop test for the next one
+static void inner_step(Solve& S, const Level& L, cudaGraphConditionalHandle loop, int use_loop) {
+  S.vec_on(L.N, *L.g, k_inner_p, L.B, (const float*)L.eb, L.pb);
+  level_apply(S, L, L.pb, L.qb, S.C.done);
+  S.vec_on(L.N, *L.g, k_dot<float>, (int)D_GAMI, (const int*)S.C.done, (const float*)L.pb, (const float*)L.qb);
+  S.scal(s_inner_alpha, L.f_rbn2, L.f_count);
+  S.vec_on(L.N, *L.g, k_inner_update, L.B, L.eb, (const float*)L.qb, L.ub, (const float*)L.pb);
+  S.scal(s_inner_check, L.n, L.eps, L.f_rbn2, loop, use_loop);
+}
+
+static void inner_loop(Solve& S, const Level& L) {
+  level_apply(S, L, L.ub, L.qb, nullptr);
+  S.vec_on(L.N, *L.g, k_inner_resid, L.B, (const float*)L.rb, (const float*)L.qb, L.eb);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FE_CUDA(cudaStreamIsCapturing(S.s, &cs));
+  if (cs != cudaStreamCaptureStatusActive) {
+    // direct launches: all n steps are issued; those after the stop return at once
+    S.scal(s_inner_check, L.n, L.eps, L.f_rbn2, (cudaGraphConditionalHandle)0, 0);
+    for (int step = 0; step < L.n; ++step) inner_step(S, L, (cudaGraphConditionalHandle)0, 0);
+    return;
+  }
+  // recorded into a graph: a while node repeats one step while the stop test
+  // says go (the body is recorded on a second stream into the node's own graph)
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t n_deps = 0;
+  cudaGraphConditionalHandle loop;
+  FE_CUDA(cudaStreamGetCaptureInfo(S.s, &cs, nullptr, &graph, &deps, &edges, &n_deps));
+  FE_CUDA(cudaGraphConditionalHandleCreate(&loop, graph, 0, 0));
+  S.scal(s_inner_check, L.n, L.eps, L.f_rbn2, loop, 1);
+  FE_CUDA(cudaStreamGetCaptureInfo(S.s, &cs, nullptr, &graph, &deps, &edges, &n_deps));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = loop;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  FE_CUDA(cudaGraphAddNode(&node, graph, deps, edges, n_deps, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const cudaStream_t outer = S.s;
+  FE_CUDA(cudaStreamBeginCaptureToGraph(S.w->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  S.s = S.w->body;
+  try {
+    inner_step(S, L, loop, 1);
+  } catch (...) {
+    S.s = outer;
+    cudaGraph_t g;
+    cudaStreamEndCapture(S.w->body, &g);
+    throw;
+  }
+  S.s = outer;
+  FE_CUDA(cudaStreamEndCapture(S.w->body, &body));
+  FE_CUDA(cudaStreamUpdateCaptureDependencies(S.s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+}
+
+// the FCG outer iteration (Alg. 1(a) lines 9-29; lines 12-14, level 2, dropped,
+// and lines 11, 15-16, level 1, only when the coarse level is on)
 static void fcg_iteration(Solve& S) {
   SolverWork* w = S.w;
   fe_mesh* m = S.m;
   const float* B32 = m->binv32.as<float>();
   S.scal(s_outer_begin);
   S.vec(k_cast_start, B32, w->r.as<double>(), w->rb.as<float>(), w->ub.as<float>());
-  ebe_apply<float>(m, S.R, w->ub.as<float>(), w->qb.as<float>(), S.s);
-  S.vec(k_inner_resid, B32, w->rb.as<float>(), w->qb.as<float>(), w->eb.as<float>());
-  for (int step = 0; step <= S.o.n_inner; ++step) {
-    S.scal(s_inner_check, step, S.o.n_inner, S.o.eps_inner);
-    if (step == S.o.n_inner) break;
-    S.vec(k_inner_p, B32, w->eb.as<float>(), w->pb.as<float>());
-    ebe_apply<float>(m, S.R, w->pb.as<float>(), w->qb.as<float>(), S.s, S.C.done);
-    S.vec(k_dot<float>, (int)D_GAMI, (const int*)S.C.done, (const float*)w->pb.as<float>(),
-          (const float*)w->qb.as<float>());
-    S.scal(s_inner_alpha);
-    S.vec(k_inner_update, B32, w->eb.as<float>(), w->qb.as<float>(), w->ub.as<float>(), w->pb.as<float>());
+  if (S.N1 > 0) {
+    Level L1{S.N1, &S.g1, m->coarse.binv32.as<float>(), w->rb1.as<float>(), w->ub1.as<float>(),
+             w->eb1.as<float>(), w->pb1.as<float>(), w->qb1.as<float>(), true, S.o.n_inner1, S.o.eps_inner1,
+             (int)D_RBN21, (int)I_INNER1};
+    coarse_restrict<float>(m, S.R, w->rb.as<float>(), L1.rb, S.s);
+    coarse_restrict<float>(m, S.R, w->ub.as<float>(), L1.ub, S.s);
+    S.vec_on(L1.N, *L1.g, k_dot<float>, (int)D_RBN21, (const int*)nullptr, (const float*)L1.rb,
+             (const float*)L1.rb);
+    inner_loop(S, L1);
+    coarse_prolong<float>(m, S.R, (const float*)L1.ub, w->ub.as<float>(), S.s);
+    S.scal(s_level_begin);
   }
+  Level L0{S.N, &S.g, B32, w->rb.as<float>(), w->ub.as<float>(), w->eb.as<float>(), w->pb.as<float>(),
+           w->qb.as<float>(), false, S.o.n_inner, S.o.eps_inner, (int)D_RBN2, (int)I_INNER};
+  inner_loop(S, L0);
   S.vec(k_outer_zq, (const float*)w->ub.as<float>(), (const double*)w->q.as<double>());
   S.scal(s_outer_beta, S.o.literal_beta);
   S.vec(k_outer_p, (const float*)w->ub.as<float>(), w->p.as<double>());
@@ -910,6 +1041,18 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   S.u = u;
   S.o = o;
   const bool pcg = o.solver == FE_SOLVER_PCG64;
+  if (o.solver == FE_SOLVER_FCG_MG) {
+    build_coarse_jacobi(m, s);
+    S.N1 = m->coarse.n_nodes;
+    S.g1 = vgeom(S.N1, R, sms);
+    const size_t v1 = (size_t)S.N1 * R * 3 * sizeof(float);
+    for (DevBuf* b : {&w->rb1, &w->ub1, &w->eb1, &w->pb1, &w->qb1})
+      if (b->bytes != v1) {
+        b->release();
+        b->alloc(v1);
+      }
+    FE_CUDA(cudaMemsetAsync(w->pb1.ptr, 0, v1, s));
+  }
 
   if (many) {
     // the first R cases into the slots (idle slots hold f = 0 and stay inactive)
@@ -999,7 +1142,7 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
             many->stats[cs].inner_iters = hi[I_INNER * R + r];
             many->stats[cs].relres = rel;
             many->stats[cs].status = st;
-            many->stats[cs].pad = 0;
+            many->stats[cs].inner1_iters = hi[I_INNER1 * R + r];
           }
           if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
           else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
@@ -1051,7 +1194,7 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
         stats[c].inner_iters = hi[I_INNER * R + c];
         stats[c].relres = rel;
         stats[c].status = st;
-        stats[c].pad = 0;
+        stats[c].inner1_iters = hi[I_INNER1 * R + c];
       }
       if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
       else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
@@ -1069,6 +1212,19 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   return result;
 }
 
+static void check_opts(const fe_solve_opts& o) {
+  FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED || o.solver == FE_SOLVER_FCG_MG,
+             "unknown solver %d", o.solver);
+  FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
+  FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
+  FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
+  FE_REQUIRE(o.eps_inner >= 0.0, "eps_inner must be >= 0");
+  if (o.solver == FE_SOLVER_FCG_MG) {
+    FE_REQUIRE(o.n_inner1 >= 0 && o.n_inner1 <= 100000, "n_inner1 out of range");
+    FE_REQUIRE(o.eps_inner1 >= 0.0, "eps_inner1 must be >= 0");
+  }
+}
+
 }  // namespace fe
 
 extern "C" fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* f, double* u,
@@ -1081,11 +1237,7 @@ extern "C" fe_status fe_pcg_solve(const fe_mesh* mesh, int32_t R, const double* 
     fe_solve_opts o;
     fe_solve_opts_default(&o);
     if (opts) o = *opts;
-    FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED, "unknown solver %d", o.solver);
-    FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
-    FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
-    FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
-    FE_REQUIRE(o.eps_inner >= 0.0, "eps_inner must be >= 0");
+    fe::check_opts(o);
     fe_mesh* m = const_cast<fe_mesh*>(mesh);
     fe::DeviceGuard dg(m->device);
     return fe::run_solve(m, R, f, u, o, stats, (cudaStream_t)stream);
@@ -1136,10 +1288,7 @@ extern "C" fe_status fe_solve_many(const fe_mesh* mesh, int32_t n_cases, const d
     fe_solve_opts o;
     fe_solve_opts_default(&o);
     if (opts) o = *opts;
-    FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED, "unknown solver %d", o.solver);
-    FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
-    FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
-    FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
+    fe::check_opts(o);
     fe_mesh* m = const_cast<fe_mesh*>(mesh);
     fe::DeviceGuard dg(m->device);
     const int R = R_slots > 0 ? (R_slots < n_cases ? R_slots : n_cases) : fe::choose_slots(m, n_cases);

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libfe.so")
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT = range(7)
 FE_F64, FE_F32 = 0, 1
-FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED = 0, 1
+FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED, FE_SOLVER_FCG_MG = 0, 1, 2
+SOLVERS = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED, "fcg_mg": FE_SOLVER_FCG_MG}
 EBE_DIRECT, EBE_TILED = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
@@ -28,7 +29,8 @@ STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "F
 EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_create", "fe_mesh_destroy",
             "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
             "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
-            "fe_block_jacobi_noalloc", "fe_adjoint_grad"]
+            "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
+            "fe_coarse_prolong", "fe_coarse_block_jacobi"]
 
 
 class FeError(RuntimeError):
@@ -40,12 +42,13 @@ class FeError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("n_inner", ctypes.c_int32), ("eps_inner", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32)]
+                ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32),
+                ("n_inner1", ctypes.c_int32), ("eps_inner1", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("inner1_iters", ctypes.c_int32)]
 
 
 _lib = None
@@ -82,9 +85,15 @@ def load(path: Optional[str] = None):
                                   ctypes.POINTER(_i32), _vp]
     lib.fe_block_jacobi.argtypes = [_vp, _vp, _vp]
     lib.fe_block_jacobi_noalloc.argtypes = [_vp, _vp, _vp]
+    lib.fe_coarse_info.argtypes = [_vp, ctypes.POINTER(_i64), _vp, _vp]
+    lib.fe_ebe4_apply.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    lib.fe_coarse_restrict.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    lib.fe_coarse_prolong.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    lib.fe_coarse_block_jacobi.argtypes = [_vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
-                 "fe_block_jacobi_noalloc", "fe_adjoint_grad"):
+                 "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
+                 "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -218,7 +227,7 @@ class Mesh:
     # ---- solvers --------------------------------------------------------
     def solve(self, f, u0=None, solver: str = "fcg_mixed", tol: float = 1e-8, max_outer: int = 20000,
               n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
-              check_every: int = 1, raise_on_fail: bool = True):
+              check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, raise_on_fail: bool = True):
         """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status)."""
         torch = _torch()
         R = int(f.shape[1])
@@ -227,19 +236,21 @@ class Mesh:
         up = _dev_ptr(u, torch.float64, (self.n_nodes, R, 3), name="u")
         o = SolveOpts()
         load().fe_solve_opts_default(ctypes.byref(o))
-        o.solver = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED}[solver]
+        o.solver = SOLVERS[solver]
         o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
         o.use_graph, o.literal_beta, o.check_every = int(bool(use_graph)), int(bool(literal_beta)), int(check_every)
+        o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         stats = (SolveStats * R)()
         st = load().fe_pcg_solve(self._h, R, fp, up, ctypes.byref(o), stats, self._stream())
-        out = [dict(outer=s.outer_iters, inner=s.inner_iters, relres=s.relres, status=s.status) for s in stats]
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, relres=s.relres,
+                    status=s.status) for s in stats]
         if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
             _check(st, "fe_pcg_solve")
         return u, out, st
 
     def solve_many(self, f_cases, R_slots: int = 0, solver: str = "fcg_mixed", tol: float = 1e-8,
                    max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
-                   raise_on_fail: bool = True):
+                   n_inner1: int = 300, eps_inner1: float = 0.05, raise_on_fail: bool = True):
         """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
         in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
         torch = _torch()
@@ -248,14 +259,16 @@ class Mesh:
         u = torch.empty_like(f_cases)
         o = SolveOpts()
         load().fe_solve_opts_default(ctypes.byref(o))
-        o.solver = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED}[solver]
+        o.solver = SOLVERS[solver]
         o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
         o.use_graph = int(bool(use_graph))
+        o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         stats = (SolveStats * n)()
         r_used = _i32()
         st = load().fe_solve_many(self._h, n, fp, ctypes.c_void_p(u.data_ptr()), int(R_slots), ctypes.byref(o),
                                   stats, ctypes.byref(r_used), self._stream())
-        out = [dict(outer=s.outer_iters, inner=s.inner_iters, relres=s.relres, status=s.status) for s in stats]
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, relres=s.relres,
+                    status=s.status) for s in stats]
         if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
             _check(st, "fe_solve_many")
         return u, out, st, r_used.value
@@ -265,6 +278,56 @@ class Mesh:
         torch = _torch()
         out = torch.empty((self.n_nodes, 3, 3), dtype=torch.float64, device=f"cuda:{self.device}")
         _check(load().fe_block_jacobi(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()), "fe_block_jacobi")
+        return out
+
+    # ---- TET4 coarse level (level 1) -------------------------------------
+    def coarse_info(self):
+        """(N4, vertex): coarse node count and the TET10 node id of each coarse node."""
+        n4 = _i64()
+        _check(load().fe_coarse_info(self._h, ctypes.byref(n4), None, self._stream()), "fe_coarse_info")
+        vertex = np.empty(n4.value, dtype=np.int32)
+        _check(load().fe_coarse_info(self._h, ctypes.byref(n4), vertex.ctypes.data, self._stream()),
+               "fe_coarse_info")
+        self.n_nodes4 = int(n4.value)
+        return self.n_nodes4, vertex
+
+    def _n4(self) -> int:
+        if getattr(self, "n_nodes4", None) is None:
+            self.coarse_info()
+        return self.n_nodes4
+
+    def _coarse_vec(self, fn: str, x, n_in: int, n_out: int):
+        torch = _torch()
+        if x.dim() != 3 or x.shape[0] != n_in or x.shape[2] != 3:
+            raise ValueError(f"input must be [{n_in}, R, 3]")
+        R = int(x.shape[1])
+        dt = {torch.float64: FE_F64, torch.float32: FE_F32}.get(x.dtype)
+        if dt is None:
+            raise TypeError("input must be float64 or float32")
+        y = torch.empty((n_out, R, 3), dtype=x.dtype, device=x.device)
+        _check(getattr(load(), fn)(self._h, R, dt, _dev_ptr(x, x.dtype, name="input"),
+                                   ctypes.c_void_p(y.data_ptr()), self._stream()), fn)
+        return y
+
+    def ebe4(self, x4):
+        """y4 = K1_bc x4 on the TET4 coarse mesh, x4 [N4, R, 3]."""
+        n4 = self._n4()
+        return self._coarse_vec("fe_ebe4_apply", x4, n4, n4)
+
+    def coarse_restrict(self, r10):
+        """r4 = P (P1^T r10): [N, R, 3] -> [N4, R, 3]."""
+        return self._coarse_vec("fe_coarse_restrict", r10, self.n_nodes, self._n4())
+
+    def coarse_prolong(self, u4):
+        """u10 = P (P1 u4): [N4, R, 3] -> [N, R, 3]."""
+        return self._coarse_vec("fe_coarse_prolong", u4, self._n4(), self.n_nodes)
+
+    def coarse_block_jacobi(self):
+        """Inverse 3x3 diagonal blocks of K1_bc, float64 [N4, 3, 3]."""
+        torch = _torch()
+        out = torch.empty((self._n4(), 3, 3), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(load().fe_coarse_block_jacobi(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()),
+               "fe_coarse_block_jacobi")
         return out
 
     def adjoint_grad(self, u, lam):
