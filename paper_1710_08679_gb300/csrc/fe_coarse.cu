@@ -28,18 +28,66 @@ __global__ void __launch_bounds__(kThreads) zero4_kernel(int64_t n, T* __restric
     y[i] = T(0);
 }
 
-// thread = (element, case); the element geometry comes from the TET10 corner
-// coordinates (the same corners), the vector entries from the coarse numbering
-template <typename T>
+// W consecutive cases of one node: 3W contiguous values. For float with W = 4
+// they are 48 bytes at a 48-byte multiple from a 16-byte aligned base (R is a
+// multiple of 4), moved as three 16-byte vectors.
+template <typename T, int W>
+struct CaseGroup {
+  static __device__ __forceinline__ void load(const T* __restrict__ p, T v[3 * W]) {
+#pragma unroll
+    for (int i = 0; i < 3 * W; ++i) v[i] = __ldg(p + i);
+  }
+  static __device__ __forceinline__ void store(T* p, const T v[3 * W]) {
+#pragma unroll
+    for (int i = 0; i < 3 * W; ++i) p[i] = v[i];
+  }
+  static __device__ __forceinline__ void add(T* p, const T v[3 * W]) {
+#pragma unroll
+    for (int i = 0; i < 3 * W; ++i) atomicAdd(p + i, v[i]);
+  }
+};
+
+template <>
+struct CaseGroup<float, 4> {
+  static __device__ __forceinline__ void load(const float* __restrict__ p, float v[12]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 t = __ldg(q + k);
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+  }
+  static __device__ __forceinline__ void store(float* p, const float v[12]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  }
+  static __device__ __forceinline__ void add(float* p, const float v[12]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(q + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+  }
+};
+
+// thread = (element, group of W cases); geometry from the TET10 corner
+// coordinates (the same corners), vector entries in the coarse numbering.
+// Fixed DOFs: the element that owns the corner adds x (y starts at zero), the
+// others add zero, so y = x there.
+template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, const int32_t* __restrict__ conn4,
                                                         const uint8_t* __restrict__ nmask4,
                                                         const uint8_t* __restrict__ own4, const T* __restrict__ x,
                                                         T* __restrict__ y, const int* __restrict__ skip) {
+  using CG = CaseGroup<T, W>;
   if (skip && *skip) return;
+  const int G = R / W;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= M.n_elem * R) return;
-  const int64_t e = gid / R;
-  const int r = (int)(gid - e * R);
+  if (gid >= M.n_elem * G) return;
+  const int64_t e = gid / G;
+  const int r0 = (int)(gid - e * G) * W;
   const int4 c4 = __ldg(reinterpret_cast<const int4*>(conn4) + e);
   const int2 c01 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e));
   const int2 c23 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e) + 1);
@@ -49,103 +97,122 @@ __global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, co
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int i = 0; i < 3; ++i) xc[k][i] = __ldg(M.xyz + 3 * (int64_t)cf[k] + i);
-  ElemGeo<T> G;
-  elem_geometry(xc[0], xc[1], xc[2], xc[3], __ldg(M.mat + 2 * e), __ldg(M.mat + 2 * e + 1), G);
+  ElemGeo<T> G4;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], __ldg(M.mat + 2 * e), __ldg(M.mat + 2 * e + 1), G4);
   const int nd[4] = {c4.x, c4.y, c4.z, c4.w};
   int mk[4];
-  T H[3][3];
+  T H[W][3][3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) H[a][b] = T(0);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    mk[k] = __ldg(nmask4 + nd[k]);
-    const T* xa = x + ((int64_t)nd[k] * R + r) * 3;
-    T u[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = ((mk[k] >> c) & 1) ? __ldg(xa + c) : T(0);
+  for (int w = 0; w < W; ++w)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) H[a][b] += u[a] * G.g[k][b];
+      for (int b = 0; b < 3; ++b) H[w][a][b] = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    mk[k] = __ldg(nmask4 + nd[k]);
+    T u[3 * W];
+    CG::load(x + ((int64_t)nd[k] * R + r0) * 3, u);
+#pragma unroll
+    for (int i = 0; i < 3 * W; ++i)
+      if (!((mk[k] >> (i % 3)) & 1)) u[i] = T(0);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) H[w][a][b] += u[3 * w + a] * G4.g[k][b];
   }
-  // V = 20 c; fold V into the stress
-  const T V = T(20) * G.c;
-  const T lt = G.lam * (H[0][0] + H[1][1] + H[2][2]);
-  T sg[6];
-  sg[0] = V * (lt + T(2) * G.mu * H[0][0]);
-  sg[1] = V * (lt + T(2) * G.mu * H[1][1]);
-  sg[2] = V * (lt + T(2) * G.mu * H[2][2]);
-  sg[3] = V * G.mu * (H[1][2] + H[2][1]);
-  sg[4] = V * G.mu * (H[0][2] + H[2][0]);
-  sg[5] = V * G.mu * (H[0][1] + H[1][0]);
+  // V = 20 c, folded into the stress
+  const T V = T(20) * G4.c;
+  T sg[W][6];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const T lt = G4.lam * (H[w][0][0] + H[w][1][1] + H[w][2][2]);
+    sg[w][0] = V * (lt + T(2) * G4.mu * H[w][0][0]);
+    sg[w][1] = V * (lt + T(2) * G4.mu * H[w][1][1]);
+    sg[w][2] = V * (lt + T(2) * G4.mu * H[w][2][2]);
+    sg[w][3] = V * G4.mu * (H[w][1][2] + H[w][2][1]);
+    sg[w][4] = V * G4.mu * (H[w][0][2] + H[w][2][0]);
+    sg[w][5] = V * G4.mu * (H[w][0][1] + H[w][1][0]);
+  }
   const int ow = __ldg(own4 + e);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    T w[3];
-    sym_mv(sg, G.g[k], w);
-    T* ya = y + ((int64_t)nd[k] * R + r) * 3;
+    T out[3 * W];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if ((mk[k] >> c) & 1)
-        atomicAdd(ya + c, w[c]);
-      else if ((ow >> k) & 1)
-        ya[c] = __ldg(x + ((int64_t)nd[k] * R + r) * 3 + c);
+    for (int w = 0; w < W; ++w) sym_mv(sg[w], G4.g[k], out + 3 * w);
+    T* ya = y + ((int64_t)nd[k] * R + r0) * 3;
+    if (mk[k] != 7) {
+      const T* xa = x + ((int64_t)nd[k] * R + r0) * 3;
+#pragma unroll
+      for (int i = 0; i < 3 * W; ++i)
+        if (!((mk[k] >> (i % 3)) & 1)) out[i] = ((ow >> k) & 1) ? __ldg(xa + i) : T(0);
     }
+    CG::add(ya, out);
   }
 }
 
-// r4 = P1^T r10 (r4 zeroed before), constrained coarse DOFs skipped (stay zero)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) restrict_kernel(int64_t N10, int R, const int32_t* __restrict__ ends,
+// r4 = P (P1^T r10), gathered per coarse node: its own vertex value plus half of
+// each edge node it ends (the adjacency is built once on the host), so no
+// atomics and no zeroing pass.
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) restrict_kernel(int64_t N4, int R, const int32_t* __restrict__ vertex,
+                                                            const int32_t* __restrict__ adj_ptr,
+                                                            const int32_t* __restrict__ adj,
                                                             const uint8_t* __restrict__ nmask4,
                                                             const T* __restrict__ r10, T* __restrict__ r4,
                                                             const int* __restrict__ skip) {
+  using CG = CaseGroup<T, W>;
   if (skip && *skip) return;
+  const int G = R / W;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= N10 * R) return;
-  const int64_t n = gid / R;
-  const int r = (int)(gid - n * R);
-  const int2 ab = __ldg(reinterpret_cast<const int2*>(ends) + n);
-  const T* v = r10 + gid * 3;
-  const int ma = __ldg(nmask4 + ab.x);
-  if (ab.x == ab.y) {
+  if (gid >= N4 * G) return;
+  const int64_t a = gid / G;
+  const int r0 = (int)(gid - a * G) * W;
+  T acc[3 * W], v[3 * W];
+  CG::load(r10 + ((int64_t)__ldg(vertex + a) * R + r0) * 3, acc);
+  const int j1 = __ldg(adj_ptr + a + 1);
+  for (int j = __ldg(adj_ptr + a); j < j1; ++j) {
+    CG::load(r10 + ((int64_t)__ldg(adj + j) * R + r0) * 3, v);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if ((ma >> c) & 1) atomicAdd(r4 + ((int64_t)ab.x * R + r) * 3 + c, v[c]);
-  } else {
-    const int mb = __ldg(nmask4 + ab.y);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T h = T(0.5) * v[c];
-      if ((ma >> c) & 1) atomicAdd(r4 + ((int64_t)ab.x * R + r) * 3 + c, h);
-      if ((mb >> c) & 1) atomicAdd(r4 + ((int64_t)ab.y * R + r) * 3 + c, h);
-    }
+    for (int i = 0; i < 3 * W; ++i) acc[i] += T(0.5) * v[i];
   }
+  const int mk = __ldg(nmask4 + a);
+#pragma unroll
+  for (int i = 0; i < 3 * W; ++i)
+    if (!((mk >> (i % 3)) & 1)) acc[i] = T(0);
+  CG::store(r4 + gid * 3 * W, acc);
 }
 
 // u10 = P u4: vertex values copied, edge nodes the mean of their ends, then the
 // fine Dirichlet DOFs zeroed
-template <typename T>
+template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) prolong_kernel(int64_t N10, int R, const int32_t* __restrict__ ends,
                                                            const uint8_t* __restrict__ nmask,
                                                            const T* __restrict__ u4, T* __restrict__ u10,
                                                            const int* __restrict__ skip) {
+  using CG = CaseGroup<T, W>;
   if (skip && *skip) return;
+  const int G = R / W;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= N10 * R) return;
-  const int64_t n = gid / R;
-  const int r = (int)(gid - n * R);
+  if (gid >= N10 * G) return;
+  const int64_t n = gid / G;
+  const int r0 = (int)(gid - n * G) * W;
   const int2 ab = __ldg(reinterpret_cast<const int2*>(ends) + n);
   const int mk = __ldg(nmask + n);
-  const T* a = u4 + ((int64_t)ab.x * R + r) * 3;
-  const T* b = u4 + ((int64_t)ab.y * R + r) * 3;
+  T va[3 * W];
+  CG::load(u4 + ((int64_t)ab.x * R + r0) * 3, va);
+  if (ab.x != ab.y) {
+    T vb[3 * W];
+    CG::load(u4 + ((int64_t)ab.y * R + r0) * 3, vb);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const T v = (ab.x == ab.y) ? a[c] : T(0.5) * (a[c] + b[c]);
-    u10[gid * 3 + c] = ((mk >> c) & 1) ? v : T(0);
+    for (int i = 0; i < 3 * W; ++i) va[i] = T(0.5) * (va[i] + vb[i]);
   }
+#pragma unroll
+  for (int i = 0; i < 3 * W; ++i)
+    if (!((mk >> (i % 3)) & 1)) va[i] = T(0);
+  CG::store(u10 + gid * 3 * W, va);
 }
 
 // diagonal 3x3 blocks of K1: V [(lam + mu) g_a g_a^T + mu |g_a|^2 I] per corner
@@ -250,17 +317,38 @@ void build_coarse(fe_mesh* m, cudaStream_t s) {
     FE_REQUIRE(ends[(size_t)(2 * n)] >= 0, "node %lld belongs to no element (no coarse interpolation)",
                (long long)n);
   for (int64_t v = 0; v < N4; ++v) mk4[(size_t)v] = m->nmask_host[(size_t)vertex[(size_t)v]];
+  // coarse node -> the edge nodes it ends (counting sort over the fine nodes)
+  std::vector<int32_t> adj_ptr((size_t)N4 + 1, 0), adj;
+  for (int64_t n = 0; n < N; ++n)
+    if (ends[(size_t)(2 * n)] != ends[(size_t)(2 * n + 1)]) {
+      ++adj_ptr[(size_t)ends[(size_t)(2 * n)] + 1];
+      ++adj_ptr[(size_t)ends[(size_t)(2 * n + 1)] + 1];
+    }
+  for (int64_t v = 0; v < N4; ++v) adj_ptr[(size_t)v + 1] += adj_ptr[(size_t)v];
+  adj.resize((size_t)adj_ptr[(size_t)N4]);
+  {
+    std::vector<int32_t> fill(adj_ptr.begin(), adj_ptr.end() - 1);
+    for (int64_t n = 0; n < N; ++n)
+      if (ends[(size_t)(2 * n)] != ends[(size_t)(2 * n + 1)]) {
+        adj[(size_t)fill[(size_t)ends[(size_t)(2 * n)]]++] = (int32_t)n;
+        adj[(size_t)fill[(size_t)ends[(size_t)(2 * n + 1)]]++] = (int32_t)n;
+      }
+  }
   c.n_nodes = N4;
   c.conn4.alloc(conn4.size() * 4);
   c.ends.alloc(ends.size() * 4);
   c.nmask4.alloc(mk4.size());
   c.own4.alloc(own4.size());
   c.vertex.alloc(vertex.size() * 4);
+  c.adj_ptr.alloc(adj_ptr.size() * 4);
+  c.adj.alloc(std::max<size_t>(adj.size(), 1) * 4);
   FE_CUDA(cudaMemcpyAsync(c.conn4.ptr, conn4.data(), conn4.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(c.ends.ptr, ends.data(), ends.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(c.nmask4.ptr, mk4.data(), mk4.size(), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(c.own4.ptr, own4.data(), own4.size(), cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(c.vertex.ptr, vertex.data(), vertex.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(c.adj_ptr.ptr, adj_ptr.data(), adj_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!adj.empty()) FE_CUDA(cudaMemcpyAsync(c.adj.ptr, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaStreamSynchronize(s));
   c.ready = true;
   c.jacobi_ready = false;
@@ -291,6 +379,13 @@ void build_coarse_jacobi(fe_mesh* m, cudaStream_t s) {
   c.jacobi_ready = true;
 }
 
+// W = 4 cases per thread where the FP32 case groups are 16-byte vectors (R a
+// multiple of 4), else one case per thread.
+template <typename T>
+static int case_group(int R) {
+  return (sizeof(T) == 4 && R % 4 == 0) ? 4 : 1;
+}
+
 template <typename T>
 void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
@@ -298,9 +393,18 @@ void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, con
   const int64_t n4 = c.n_nodes * (int64_t)R * 3;
   zero4_kernel<T><<<std::min<unsigned>(blocks_for(n4), 152 * 16), kThreads, 0, s>>>(n4, y4, skip);
   FE_CHECK_LAUNCH();
-  ebe4_kernel<T><<<blocks_for(m->n_elem * R), kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(),
-                                                                 c.nmask4.as<uint8_t>(), c.own4.as<uint8_t>(), x4, y4,
-                                                                 skip);
+  const int W = case_group<T>(R);
+  const unsigned grid = blocks_for(m->n_elem * (R / W));
+  if constexpr (sizeof(T) == 4) {
+    if (W == 4) {
+      ebe4_kernel<T, 4><<<grid, kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(), c.nmask4.as<uint8_t>(),
+                                                  c.own4.as<uint8_t>(), x4, y4, skip);
+      FE_CHECK_LAUNCH();
+      return;
+    }
+  }
+  ebe4_kernel<T, 1><<<grid, kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(), c.nmask4.as<uint8_t>(),
+                                                c.own4.as<uint8_t>(), x4, y4, skip);
   FE_CHECK_LAUNCH();
 }
 
@@ -308,11 +412,18 @@ template <typename T>
 void coarse_restrict(const fe_mesh* m, int R, const T* r10, T* r4, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
   FE_REQUIRE(c.ready, "coarse level not built");
-  const int64_t n4 = c.n_nodes * (int64_t)R * 3;
-  zero4_kernel<T><<<std::min<unsigned>(blocks_for(n4), 152 * 16), kThreads, 0, s>>>(n4, r4, skip);
-  FE_CHECK_LAUNCH();
-  restrict_kernel<T><<<blocks_for(m->n_nodes * R), kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(),
-                                                                      c.nmask4.as<uint8_t>(), r10, r4, skip);
+  const int W = case_group<T>(R);
+  const unsigned grid = blocks_for(c.n_nodes * (R / W));
+  if constexpr (sizeof(T) == 4) {
+    if (W == 4) {
+      restrict_kernel<T, 4><<<grid, kThreads, 0, s>>>(c.n_nodes, R, c.vertex.as<int32_t>(), c.adj_ptr.as<int32_t>(),
+                                                      c.adj.as<int32_t>(), c.nmask4.as<uint8_t>(), r10, r4, skip);
+      FE_CHECK_LAUNCH();
+      return;
+    }
+  }
+  restrict_kernel<T, 1><<<grid, kThreads, 0, s>>>(c.n_nodes, R, c.vertex.as<int32_t>(), c.adj_ptr.as<int32_t>(),
+                                                    c.adj.as<int32_t>(), c.nmask4.as<uint8_t>(), r10, r4, skip);
   FE_CHECK_LAUNCH();
 }
 
@@ -320,8 +431,18 @@ template <typename T>
 void coarse_prolong(const fe_mesh* m, int R, const T* u4, T* u10, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
   FE_REQUIRE(c.ready, "coarse level not built");
-  prolong_kernel<T><<<blocks_for(m->n_nodes * R), kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(),
-                                                                     m->nmask.as<uint8_t>(), u4, u10, skip);
+  const int W = case_group<T>(R);
+  const unsigned grid = blocks_for(m->n_nodes * (R / W));
+  if constexpr (sizeof(T) == 4) {
+    if (W == 4) {
+      prolong_kernel<T, 4><<<grid, kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(), m->nmask.as<uint8_t>(), u4,
+                                                     u10, skip);
+      FE_CHECK_LAUNCH();
+      return;
+    }
+  }
+  prolong_kernel<T, 1><<<grid, kThreads, 0, s>>>(m->n_nodes, R, c.ends.as<int32_t>(), m->nmask.as<uint8_t>(), u4,
+                                                   u10, skip);
   FE_CHECK_LAUNCH();
 }
 
@@ -356,6 +477,7 @@ fe_mesh* coarse_args(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void*
   FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range [1, 64]", R);
   FE_REQUIRE(dtype == FE_F32 || dtype == FE_F64, "dtype must be FE_F32 or FE_F64");
   FE_REQUIRE(in != out, "input and output must not alias");
+  FE_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0, "vectors must be 16-byte aligned");
   return const_cast<fe_mesh*>(mesh);
 }
 }  // namespace

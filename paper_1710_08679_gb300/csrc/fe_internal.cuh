@@ -140,6 +140,7 @@ struct Coarse {
   DevBuf nmask4;            // uint8 [N4] free-DOF bits
   DevBuf own4;              // uint8 [E] bit a set if element e is the first holding its corner a
   DevBuf vertex;            // int32 [N4] TET10 id of each coarse node
+  DevBuf adj_ptr, adj;      // int32 [N4 + 1], [2 * edge nodes]: edge nodes ending at each coarse node
   bool jacobi_ready = false;
   DevBuf binv64, binv32;    // [N4][9] inverse diagonal blocks of K1_bc
 };

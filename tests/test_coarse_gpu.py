@@ -68,9 +68,9 @@ def test_ebe4_matches_assembled_tet4_operator(meshes, name, R, dtype):
 @pytest.mark.gpu
 @pytest.mark.parametrize("name", ["box8", "crust9x5x4"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_transfers_match_oracle(meshes, name, dtype):
+@pytest.mark.parametrize("R", [5, 8])
+def test_transfers_match_oracle(meshes, name, dtype, R):
     m, cm, M = meshes[name]
-    R = 5
     tdt = torch.float32 if dtype == "f32" else torch.float64
     tol = 2e-6 if dtype == "f32" else 1e-15
     r10 = mg.random_vectors(m.n_nodes, R, seed=41)
