@@ -228,7 +228,7 @@ fe_status fe_solve_many(const fe_mesh* mesh, int32_t n_cases, const double* f_de
 
 /*
  * fe_block_jacobi -- the 3x3 block-Jacobi preconditioner M^-1 = diag3x3[K_bc]^-1
- * of Algorithm 1 (lines 1-3) and of the PCG baseline, built on first use from
+ * of Algorithm 1 and of the PCG baseline, built on first use from
  * the element matrices' diagonal blocks (closed form, FP64) with constrained
  * rows and columns set to the identity.
  *   binv_dev  device double [N][3][3], overwritten with the inverse blocks
@@ -269,7 +269,7 @@ fe_status fe_adjoint_grad(const fe_mesh* mesh, int32_t R, const double* u_dev, c
                           double* g_elem_dev, void* stream);
 
 /*
- * TET4 coarse level (Sec. 2 and Algorithm 1 lines 2, 11, 15-16: inner loop level 1).
+ * TET4 coarse level (Sec. 2 and Algorithm 1(a): inner loop level 1).
  * The coarse mesh is the TET10 mesh without its edge nodes: same elements and
  * materials, first-order shape functions. Its nodes are the corner nodes of the
  * TET10 mesh numbered in increasing TET10 id (internal numbering of this
@@ -308,7 +308,7 @@ fe_status fe_coarse_prolong(const fe_mesh* mesh, int32_t R, fe_dtype dtype, cons
                             void* stream);
 
 /* fe_coarse_block_jacobi -- the level-1 block Jacobi M1^-1 = diag3x3[K1_bc]^-1
- * (Algorithm 1 line 2) from the closed form of the TET4 diagonal blocks,
+ * (Algorithm 1(a), set-up) from the closed form of the TET4 diagonal blocks,
  * V [(lam + mu) g_a g_a^T + mu |g_a|^2 I], built on first use (FP64).
  *   binv4_dev  device double [N4][3][3], overwritten
  * Fails with FE_EINVAL if a free coarse node has a singular block. */

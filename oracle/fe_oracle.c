@@ -18,7 +18,7 @@
  *     replaced by identity: K_bc = P K P + (I - P);
  *   - y = K_bc x for R vectors stored [node][R][3] (the multiple-vector layout
  *     of Sec. 3.1);
- *   - 3x3 block Jacobi M = diag[K_bc] (Algorithm 1, lines 1-3);
+ *   - 3x3 block Jacobi M = diag[K_bc] (Algorithm 1(a), its set-up);
  *   - preconditioned CG with 3x3 block Jacobi (the PCGE baseline of Sec. 4);
  *   - the flexible (adaptive) CG of Algorithm 1(a) with the FP32 inner PCG of
  *     Algorithm 1(b) at level 0, for R cases at once;
@@ -496,7 +496,7 @@ int oracle_sampled_product(int64_t N, const double* coords, int64_t E, const int
 /* 3x3 block Jacobi                                                           */
 /* ------------------------------------------------------------------------- */
 
-/* Minv[N][9] = inverse of the diagonal 3x3 block of K_bc per node (Alg. 1, lines 1-3). */
+/* Minv[N][9] = inverse of the diagonal 3x3 block of K_bc per node (Algorithm 1(a), set-up). */
 int oracle_block_jacobi(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, double* Minv) {
   for (int64_t n = 0; n < N; ++n) {
     int64_t b = find_block(rowptr, col, (int32_t)n, (int32_t)n);
@@ -667,13 +667,13 @@ static int inner_pcg_f32(int64_t N, const int64_t* rowptr, const int32_t* col, c
 }
 
 /* Outer loop (FP64), per case r while ||r||/||f|| > tol (per-case masking):
- *   rbar = (float) r; ubar = Mbar^-1 rbar                               (lines 9-10)
- *   with the TET4 level (N4 > 0):
- *     rbar1 = P1^T rbar; ubar1 = P1^T ubar                              (line 11)
- *     inner loop (b) on Kbar1 ubar1 = rbar1 with eps_inner1, n_inner1   (line 15)
- *     ubar = P1 ubar1                                                   (line 16)
- *   inner loop (b) on Kbar ubar = rbar with eps_inner, n_inner          (line 17)
- *   z = (double) ubar                                                   (line 18, read as z)
+ *   rbar = (float) r; ubar = Mbar^-1 rbar
+ *   with the TET4 level (N4 > 0), inner loop level 1:
+ *     rbar1 = P1^T rbar; ubar1 = P1^T ubar
+ *     inner loop (b) on Kbar1 ubar1 = rbar1 with eps_inner1, n_inner1
+ *     ubar = P1 ubar1
+ *   inner loop level 0: (b) on Kbar ubar = rbar with eps_inner, n_inner
+ *   z = (double) ubar                                 (printed "u <= ubar", read as z)
  *   if i > 1: beta = -(z, q_prev) / (p_prev, q_prev)   (flexible CG; the paper
  *             prints gamma=(z,q), beta=gamma/rho, read as this form -- with
  *             literal_beta != 0 the printed form is used instead)
@@ -714,7 +714,7 @@ int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const do
     for (int64_t k = 0; k < 9 * N4; ++k) Minv4_32[k] = (float)Minv4[k];
   }
 
-  oracle_spmv(N, rowptr, col, vals, R, u, q);            /* lines 4-5: r = f - K u */
+  oracle_spmv(N, rowptr, col, vals, R, u, q);            /* r = f - K u */
   for (size_t k = 0; k < nv; ++k) r[k] = f[k] - q[k];
   memset(p, 0, nv * 8);
   dots(N, R, f, f, fn);

@@ -1,5 +1,6 @@
 // First-order (TET4) coarse level of the inner solve (Sec. 2: "the same mesh but
-// without edge nodes"; Algorithm 1 lines 2, 11, 15 and 16 at level 1).
+// without edge nodes"; inner loop level 1 of Algorithm 1(a): its block Jacobi,
+// the restriction of the residual and guess, and the prolongation of the result).
 //
 //  * the coarse mesh is the corner nodes of the TET10 mesh, with the same elements
 //    and materials; the element stiffness of a linear tetrahedron is

@@ -1,16 +1,17 @@
 // Solvers of K_bc u_r = f_r for R cases at once.
 //
 //  * FE_SOLVER_PCG64: CG with 3x3 block Jacobi in FP64 (the paper's PCGE
-//    reference solver of Sec. 4, Algorithm 1(a) without lines 8-17).
+//    reference solver of Sec. 4: Algorithm 1(a) with the preconditioner a
+//    single block-Jacobi application instead of the inner loops).
 //  * FE_SOLVER_FCG_MIXED: Algorithm 1 with the inner loop at level 0 only: an
 //    FP64 flexible (adaptive) CG whose preconditioner z = K^-1 r is an FP32
 //    block-Jacobi CG (Algorithm 1(b)) stopped at N steps or when
 //    max_r ||e_r||^2/||rbar_r||^2 <= eps (the max-over-cases rule of Sec. 3.1).
 //  * FE_SOLVER_FCG_MG: as FCG_MIXED with the inner loop at level 1 first: the
-//    residual and the block-Jacobi guess are restricted to the TET4 mesh
-//    (Algorithm 1 line 11), solved there by the same FP32 CG with the TET4
-//    operator and its own block Jacobi (line 15), and the coarse solution is
-//    prolonged as the initial guess of the level-0 loop (line 16).
+//    residual and the block-Jacobi guess are restricted to the TET4 mesh,
+//    solved there by the same FP32 CG with the TET4 operator and its own block
+//    Jacobi, and the coarse solution is prolonged as the initial guess of the
+//    level-0 loop (Algorithm 1(a), inner loop level 1).
 //
 // GPU design: every per-case scalar (rho, gamma, alpha, beta, norms, masks)
 // lives in device arrays of length R; kernels read them directly, so one outer
@@ -366,7 +367,7 @@ __global__ void k_pcg_p(int64_t N, Cases C, const double* __restrict__ Bi, const
   VEC_LOOP_END
 }
 
-// FCG inner start (Alg. 1(a) lines 9-10): rbar = (float) r ; ubar = Mbar^-1 rbar ;
+// FCG inner start (Algorithm 1(a)): rbar = (float) r ; ubar = Mbar^-1 rbar ;
 // rbn2 += ||rbar||^2. Inactive cases get zeros.
 __global__ void k_cast_start(int64_t N, Cases C, const float* __restrict__ Bi, const double* __restrict__ rv,
                              float* __restrict__ rb, float* __restrict__ ub) {
@@ -386,7 +387,7 @@ __global__ void k_cast_start(int64_t N, Cases C, const float* __restrict__ Bi, c
   reduce_cases((double)acc, C.R, blockDim.x / C.R, sm, C.d + D_RBN2 * C.R);
 }
 
-// Alg. 1(b) lines 1-2: e = rbar - Kbar ubar (q holds Kbar ubar); en2 += ||e||^2 ;
+// Algorithm 1(b), start: e = rbar - Kbar ubar (q holds Kbar ubar); en2 += ||e||^2 ;
 // rhoa += (Mbar^-1 e, e)
 __global__ void k_inner_resid(int64_t N, Cases C, const float* __restrict__ Bi, const float* __restrict__ rb,
                               const float* __restrict__ qb, float* __restrict__ eb) {
@@ -406,7 +407,7 @@ __global__ void k_inner_resid(int64_t N, Cases C, const float* __restrict__ Bi, 
   reduce_cases((double)a2, C.R, blockDim.x / C.R, sm, C.d + D_RHOA * C.R);
 }
 
-// Alg. 1(b) lines 6-11: pbar = Mbar^-1 e + beta pbar
+// Algorithm 1(b), search direction: pbar = Mbar^-1 e + beta pbar
 __global__ void k_inner_p(int64_t N, Cases C, const float* __restrict__ Bi, const float* __restrict__ eb,
                           float* __restrict__ pb) {
   if (*C.done) return;
@@ -422,7 +423,7 @@ __global__ void k_inner_p(int64_t N, Cases C, const float* __restrict__ Bi, cons
   VEC_LOOP_END
 }
 
-// Alg. 1(b) lines 16-17: e -= alpha q ; ubar += alpha p ; then en2, rhoa for the next step
+// Algorithm 1(b), update: e -= alpha q ; ubar += alpha p ; then en2, rhoa for the next step
 __global__ void k_inner_update(int64_t N, Cases C, const float* __restrict__ Bi, float* __restrict__ eb,
                                const float* __restrict__ qb, float* __restrict__ ub, const float* __restrict__ pb) {
   extern __shared__ double sm[];
@@ -454,7 +455,7 @@ __global__ void k_outer_zq(int64_t N, Cases C, const float* __restrict__ ub, con
   reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_ZQ * C.R);
 }
 
-// Alg. 1(a) line 23: p = z + beta p with z = (double) ubar
+// Algorithm 1(a), search direction: p = z + beta p with z = (double) ubar
 __global__ void k_outer_p(int64_t N, Cases C, const float* __restrict__ ub, double* __restrict__ p) {
   VEC_LOOP_BEGIN
   if (C.I(I_ACTIVE, r)) {
@@ -467,7 +468,7 @@ __global__ void k_outer_p(int64_t N, Cases C, const float* __restrict__ ub, doub
   VEC_LOOP_END
 }
 
-// Alg. 1(a) lines 25-26: rho += (z, r) ; gam += (p, q)
+// Algorithm 1(a): rho += (z, r) ; gam += (p, q)
 __global__ void k_outer_dots(int64_t N, Cases C, const float* __restrict__ ub, const double* __restrict__ rv,
                              const double* __restrict__ p, const double* __restrict__ q) {
   extern __shared__ double sm[];
@@ -482,7 +483,7 @@ __global__ void k_outer_dots(int64_t N, Cases C, const float* __restrict__ ub, c
   reduce_cases(a2, C.R, blockDim.x / C.R, sm, C.d + D_GAM * C.R);
 }
 
-// Alg. 1(a) lines 28-29: r -= alpha q ; u += alpha p ; rn2 += ||r||^2
+// Algorithm 1(a), update: r -= alpha q ; u += alpha p ; rn2 += ||r||^2
 __global__ void k_outer_update(int64_t N, Cases C, double* __restrict__ rv, const double* __restrict__ q,
                                double* __restrict__ u, const double* __restrict__ p) {
   extern __shared__ double sm[];
@@ -699,7 +700,7 @@ __global__ void s_level_begin(Cases C) {
   }
 }
 
-// inner stop test before the next step and inner beta (Alg. 1(b) lines 5, 8-10).
+// inner stop test before the next step and inner beta (Algorithm 1(b)).
 // The step index is the device counter; with `loop` set, the stop decision is
 // also the condition of the graph's while node that repeats the inner step, so
 // the loop ends on the device after at most n_inner steps.
@@ -730,7 +731,7 @@ __global__ void s_inner_check(Cases C, int n_inner, double eps, int f_rbn2, cuda
   }
 }
 
-// inner alpha (Alg. 1(b) lines 13-15)
+// inner alpha (Algorithm 1(b))
 __global__ void s_inner_alpha(Cases C, int f_rbn2, int f_count) {
   const int r = threadIdx.x;
   if (*C.done) return;
@@ -743,7 +744,7 @@ __global__ void s_inner_alpha(Cases C, int f_rbn2, int f_count) {
   if (C.I(I_ACTIVE, r)) C.I(f_count, r) += 1;
 }
 
-// outer beta (Alg. 1(a) lines 19-22, read as flexible CG unless literal)
+// outer beta (Algorithm 1(a), read as flexible CG unless literal)
 __global__ void s_outer_beta(Cases C, int literal) {
   const int r = threadIdx.x;
   double be = 0.0;
@@ -761,7 +762,7 @@ __global__ void s_outer_beta(Cases C, int literal) {
   C.D(D_GAM, r) = 0.0;
 }
 
-// outer alpha (Alg. 1(a) line 27) and bookkeeping
+// outer alpha (Algorithm 1(a)) and bookkeeping
 __global__ void s_outer_alpha(Cases C) {
   const int r = threadIdx.x;
   C.D(D_RN2, r) = 0.0;
@@ -782,7 +783,7 @@ __global__ void s_outer_alpha(Cases C) {
   C.I(I_OUTER, r) += 1;
 }
 
-// outer stop test (Alg. 1(a) line 8, per case) and iteration cap
+// outer stop test (Algorithm 1(a), per case) and iteration cap
 __global__ void s_outer_check(Cases C, double tol, int max_outer) {
   const int r = threadIdx.x;
   if (!C.I(I_ACTIVE, r)) return;
@@ -902,7 +903,7 @@ static void level_apply(Solve& S, const Level& L, const float* x, float* y, cons
     ebe_apply<float>(S.m, S.R, x, y, S.s, skip);
 }
 
-// one inner step (Alg. 1(b) lines 6-17) and the stop test for the next one
+// one inner step (Algorithm 1(b)) and the stop test for the next one
 static void inner_step(Solve& S, const Level& L, cudaGraphConditionalHandle loop, int use_loop) {
   S.vec_on(L.N, *L.g, k_inner_p, L.B, (const float*)L.eb, L.pb);
   level_apply(S, L, L.pb, L.qb, S.C.done);
@@ -958,8 +959,8 @@ static void inner_loop(Solve& S, const Level& L) {
   FE_CUDA(cudaStreamUpdateCaptureDependencies(S.s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
 }
 
-// the FCG outer iteration (Alg. 1(a) lines 9-29; lines 12-14, level 2, dropped,
-// and lines 11, 15-16, level 1, only when the coarse level is on)
+// the FCG outer iteration (Algorithm 1(a); inner loop level 2 dropped, inner
+// loop level 1 only when the coarse level is on)
 static void fcg_iteration(Solve& S) {
   SolverWork* w = S.w;
   fe_mesh* m = S.m;
