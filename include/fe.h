@@ -74,6 +74,10 @@ typedef struct {
   int32_t verbose;       /* reserved, 0 */
   int32_t n_inner1;      /* FCG_MG: cap on level-1 (TET4) inner steps per outer iteration (300) */
   double eps_inner1;     /* FCG_MG: level-1 inner stop, the same rule as eps_inner (0.05) */
+  int32_t coarse_op;     /* FCG_MG level-1 operator: 0 assembled when it fits, else element by
+                            element (default); 1 assembled (FE_EINVAL if it does not fit);
+                            2 element by element */
+  int32_t pad1;
 } fe_solve_opts;
 
 /* Per-case results of fe_pcg_solve. */
@@ -93,7 +97,7 @@ const char* fe_version(void);
 
 /* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
  * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1, n_inner1 300,
- * eps_inner1 0.05 (the paper's table of loop settings, levels 0 and 1). */
+ * eps_inner1 0.05 (the paper's table of loop settings, levels 0 and 1), coarse_op 0. */
 void fe_solve_opts_default(fe_solve_opts* opts);
 
 /*
@@ -296,6 +300,17 @@ fe_status fe_coarse_info(const fe_mesh* mesh, int64_t* n_nodes4, int32_t* vertex
  *   x4, y4   device [N4][R][3] of dtype, 16-byte aligned, not aliased; y4 overwritten
  * Asynchronous on `stream`. */
 fe_status fe_ebe4_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x4, void* y4, void* stream);
+
+/* fe_coarse_apply -- y4 = K1_bc x4 for R cases in FP32 with K1_bc assembled in
+ * 3x3 block CSR (FP64 assembly, FP32 values; built on first use and again after
+ * fe_mesh_set_log_young). This is the level-1 operator of the FCG_MG solver
+ * whenever the matrix (about 36 bytes per block, 15 blocks per coarse node, plus
+ * a temporary FP64 copy) fits in a quarter of the free device memory; otherwise
+ * the solver uses the element-by-element product. Fails with FE_EINVAL if the
+ * matrix does not fit.
+ *   x4, y4   device float [N4][R][3], 16-byte aligned, not aliased; y4 overwritten
+ * Asynchronous on `stream` after the first call. */
+fe_status fe_coarse_apply(const fe_mesh* mesh, int32_t R, const float* x4, float* y4, void* stream);
 
 /* fe_coarse_restrict -- r4 = P (P1^T r10): r10 device [N][R][3], r4 device
  * [N4][R][3] overwritten (fixed coarse DOFs 0). Asynchronous on `stream`. */

@@ -10,6 +10,12 @@
 //    the mean of its two ends (linear interpolation); P1^T is its transpose;
 //  * Dirichlet DOFs are kept at zero by both transfers, and the coarse operator is
 //    K1_bc = P K1 P + (I - P) with the coarse free mask.
+//  * two ways to apply K1_bc: element by element (fe_ebe4_apply), or assembled
+//    once per material state into a 3x3 block CSR matrix and applied by a
+//    multi-vector block SpMV (what the solver uses when the matrix fits). A TET4
+//    element has too little arithmetic to hide its 12 scattered node updates, so
+//    on GB300 the matrix-free product is bound by atomics and load latency, while
+//    the block SpMV reads about 36 bytes per block once for all R cases.
 #include <algorithm>
 #include <vector>
 
@@ -73,12 +79,72 @@ struct CaseGroup<float, 4> {
   }
 };
 
-// thread = (element, group of W cases); geometry from the TET10 corner
-// coordinates (the same corners), vector entries in the coarse numbering.
+// Per-element TET4 data of the FP32 products, computed once per material state:
+// grad L_0..3 (12 floats), lam V, mu V, 2 pad, from the FP32 corner coordinates.
+__global__ void __launch_bounds__(kThreads) coarse_geo_kernel(MeshView<float> M, float4* __restrict__ geo) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M.n_elem) return;
+  float xc[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xc[k][i] = M.xyz[3 * (int64_t)M.conn[10 * e + k] + i];
+  ElemGeo<float> G;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], M.mat[2 * e], M.mat[2 * e + 1], G);
+  const float V = 20.f * G.c;
+  geo[4 * e + 0] = make_float4(G.g[0][0], G.g[0][1], G.g[0][2], G.g[1][0]);
+  geo[4 * e + 1] = make_float4(G.g[1][1], G.g[1][2], G.g[2][0], G.g[2][1]);
+  geo[4 * e + 2] = make_float4(G.g[2][2], G.g[3][0], G.g[3][1], G.g[3][2]);
+  geo[4 * e + 3] = make_float4(G.lam * V, G.mu * V, 0.f, 0.f);
+}
+
+// TET4 element data for one thread: gradients and the volume-weighted Lame
+// constants, either read from the per-element buffer (FP32) or computed from the
+// corner coordinates (FP64, used for parity checks).
+template <typename T>
+struct Tet4Geo {
+  T g[4][3];
+  T lv, mv;  // lam V, mu V
+};
+
+__device__ __forceinline__ void tet4_geo(const float4* __restrict__ geo, const MeshView<float>&, int64_t e,
+                                         Tet4Geo<float>& G) {
+  const float4 a = __ldg(geo + 4 * e), b = __ldg(geo + 4 * e + 1), c = __ldg(geo + 4 * e + 2),
+               d = __ldg(geo + 4 * e + 3);
+  G.g[0][0] = a.x; G.g[0][1] = a.y; G.g[0][2] = a.z;
+  G.g[1][0] = a.w; G.g[1][1] = b.x; G.g[1][2] = b.y;
+  G.g[2][0] = b.z; G.g[2][1] = b.w; G.g[2][2] = c.x;
+  G.g[3][0] = c.y; G.g[3][1] = c.z; G.g[3][2] = c.w;
+  G.lv = d.x;
+  G.mv = d.y;
+}
+
+__device__ __forceinline__ void tet4_geo(const float4*, const MeshView<double>& M, int64_t e, Tet4Geo<double>& G) {
+  const int2 c01 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e));
+  const int2 c23 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e) + 1);
+  const int cf[4] = {c01.x, c01.y, c23.x, c23.y};
+  double xc[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xc[k][i] = __ldg(M.xyz + 3 * (int64_t)cf[k] + i);
+  ElemGeo<double> E;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], __ldg(M.mat + 2 * e), __ldg(M.mat + 2 * e + 1), E);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G.g[k][i] = E.g[k][i];
+  G.lv = E.lam * 20.0 * E.c;
+  G.mv = E.mu * 20.0 * E.c;
+}
+
+// thread = (element, group of W cases), vector entries in the coarse numbering:
+// H = sum_k u_k (x) g_k, s = lam V tr(H) I + mu V (H + H^T), y_k = s g_k.
 // Fixed DOFs: the element that owns the corner adds x (y starts at zero), the
 // others add zero, so y = x there.
 template <typename T, int W>
-__global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, const int32_t* __restrict__ conn4,
+__global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, const float4* __restrict__ geo, int R,
+                                                        const int32_t* __restrict__ conn4,
                                                         const uint8_t* __restrict__ nmask4,
                                                         const uint8_t* __restrict__ own4, const T* __restrict__ x,
                                                         T* __restrict__ y, const int* __restrict__ skip) {
@@ -90,16 +156,9 @@ __global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, co
   const int64_t e = gid / G;
   const int r0 = (int)(gid - e * G) * W;
   const int4 c4 = __ldg(reinterpret_cast<const int4*>(conn4) + e);
-  const int2 c01 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e));
-  const int2 c23 = __ldg(reinterpret_cast<const int2*>(M.conn + 10 * e) + 1);
-  const int cf[4] = {c01.x, c01.y, c23.x, c23.y};
-  T xc[4][3];
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) xc[k][i] = __ldg(M.xyz + 3 * (int64_t)cf[k] + i);
-  ElemGeo<T> G4;
-  elem_geometry(xc[0], xc[1], xc[2], xc[3], __ldg(M.mat + 2 * e), __ldg(M.mat + 2 * e + 1), G4);
+  const int ow = __ldg(own4 + e);
+  Tet4Geo<T> G4;
+  tet4_geo(geo, M, e, G4);
   const int nd[4] = {c4.x, c4.y, c4.z, c4.w};
   int mk[4];
   T H[W][3][3];
@@ -124,20 +183,17 @@ __global__ void __launch_bounds__(kThreads) ebe4_kernel(MeshView<T> M, int R, co
 #pragma unroll
         for (int b = 0; b < 3; ++b) H[w][a][b] += u[3 * w + a] * G4.g[k][b];
   }
-  // V = 20 c, folded into the stress
-  const T V = T(20) * G4.c;
   T sg[W][6];
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    const T lt = G4.lam * (H[w][0][0] + H[w][1][1] + H[w][2][2]);
-    sg[w][0] = V * (lt + T(2) * G4.mu * H[w][0][0]);
-    sg[w][1] = V * (lt + T(2) * G4.mu * H[w][1][1]);
-    sg[w][2] = V * (lt + T(2) * G4.mu * H[w][2][2]);
-    sg[w][3] = V * G4.mu * (H[w][1][2] + H[w][2][1]);
-    sg[w][4] = V * G4.mu * (H[w][0][2] + H[w][2][0]);
-    sg[w][5] = V * G4.mu * (H[w][0][1] + H[w][1][0]);
+    const T lt = G4.lv * (H[w][0][0] + H[w][1][1] + H[w][2][2]);
+    sg[w][0] = lt + T(2) * G4.mv * H[w][0][0];
+    sg[w][1] = lt + T(2) * G4.mv * H[w][1][1];
+    sg[w][2] = lt + T(2) * G4.mv * H[w][2][2];
+    sg[w][3] = G4.mv * (H[w][1][2] + H[w][2][1]);
+    sg[w][4] = G4.mv * (H[w][0][2] + H[w][2][0]);
+    sg[w][5] = G4.mv * (H[w][0][1] + H[w][1][0]);
   }
-  const int ow = __ldg(own4 + e);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     T out[3 * W];
@@ -214,6 +270,93 @@ __global__ void __launch_bounds__(kThreads) prolong_kernel(int64_t N10, int R, c
   for (int i = 0; i < 3 * W; ++i)
     if (!((mk >> (i % 3)) & 1)) va[i] = T(0);
   CG::store(u10 + gid * 3 * W, va);
+}
+
+// K1 assembly: per element the 16 blocks K_ab = V [lam g_a g_b^T + mu g_b g_a^T +
+// mu (g_a . g_b) I] added (FP64 atomics) at their block positions in row a.
+__global__ void assemble4_kernel(MeshView<double> M, const int32_t* __restrict__ conn4,
+                                 const int32_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
+                                 double* __restrict__ vals, int* __restrict__ missing) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M.n_elem) return;
+  double xc[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int i = 0; i < 3; ++i) xc[k][i] = M.xyz[3 * (int64_t)M.conn[10 * e + k] + i];
+  ElemGeo<double> G;
+  elem_geometry(xc[0], xc[1], xc[2], xc[3], M.mat[2 * e], M.mat[2 * e + 1], G);
+  const double V = 20.0 * G.c, lv = G.lam * V, mv = G.mu * V;
+  for (int a = 0; a < 4; ++a) {
+    const int ra = conn4[4 * e + a];
+    for (int b = 0; b < 4; ++b) {
+      const int cb = conn4[4 * e + b];
+      int pos = -1;
+      for (int q = rowptr[ra]; q < rowptr[ra + 1]; ++q)
+        if (cols[q] == cb) {
+          pos = q;
+          break;
+        }
+      if (pos < 0) {
+        atomicExch(missing, 1);
+        continue;
+      }
+      const double* ga = G.g[a];
+      const double* gb = G.g[b];
+      const double gg = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+      double* B = vals + 9 * (int64_t)pos;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          atomicAdd(B + 3 * i + j, lv * ga[i] * gb[j] + mv * gb[i] * ga[j] + (i == j ? mv * gg : 0.0));
+    }
+  }
+}
+
+// FP64 blocks -> FP32 blocks of K1_bc: entries coupling a fixed DOF are dropped
+// and fixed DOFs get a unit diagonal
+__global__ void mask4_blocks_kernel(int64_t N4, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
+                                    const uint8_t* __restrict__ nmask4, const double* __restrict__ v64,
+                                    float* __restrict__ v32) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= N4) return;
+  const int ma = nmask4[a];
+  for (int q = rowptr[a]; q < rowptr[a + 1]; ++q) {
+    const int b = cols[q];
+    const int mb = nmask4[b];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const bool keep = ((ma >> i) & 1) && ((mb >> j) & 1);
+        const float unit = (b == a && i == j && !((ma >> i) & 1)) ? 1.f : 0.f;
+        v32[9 * (int64_t)q + 3 * i + j] = keep ? (float)v64[9 * (int64_t)q + 3 * i + j] : unit;
+      }
+  }
+}
+
+// y4 = K1_bc x4 for R cases, thread = (row, case): the row's blocks are read by
+// the R threads of the row together (the same addresses), x by all R cases at
+// once (3R contiguous values per column node)
+__global__ void __launch_bounds__(kThreads) spmv4_kernel(int64_t N4, int R, const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ cols,
+                                                         const float* __restrict__ vals, const float* __restrict__ x,
+                                                         float* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= N4 * R) return;
+  const int64_t a = gid / R;
+  const int r = (int)(gid - a * R);
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+  const int q1 = __ldg(rowptr + a + 1);
+  for (int q = __ldg(rowptr + a); q < q1; ++q) {
+    const int64_t b = __ldg(cols + q);
+    const float* B = vals + 9 * (int64_t)q;
+    const float* xb = x + (b * R + r) * 3;
+    const float x0 = __ldg(xb), x1 = __ldg(xb + 1), x2 = __ldg(xb + 2);
+    y0 += __ldg(B + 0) * x0 + __ldg(B + 1) * x1 + __ldg(B + 2) * x2;
+    y1 += __ldg(B + 3) * x0 + __ldg(B + 4) * x1 + __ldg(B + 5) * x2;
+    y2 += __ldg(B + 6) * x0 + __ldg(B + 7) * x1 + __ldg(B + 8) * x2;
+  }
+  float* ya = y + gid * 3;
+  ya[0] = y0;
+  ya[1] = y1;
+  ya[2] = y2;
 }
 
 // diagonal 3x3 blocks of K1: V [(lam + mu) g_a g_a^T + mu |g_a|^2 I] per corner
@@ -382,6 +525,91 @@ void build_coarse_jacobi(fe_mesh* m, cudaStream_t s) {
 
 // W = 4 cases per thread where the FP32 case groups are 16-byte vectors (R a
 // multiple of 4), else one case per thread.
+void build_coarse_geometry(fe_mesh* m, cudaStream_t s) {
+  build_coarse(m, s);
+  Coarse& c = m->coarse;
+  if (c.geo_ready) return;
+  if (!c.geo32.ptr) c.geo32.alloc((size_t)m->n_elem * 16 * sizeof(float));
+  coarse_geo_kernel<<<blocks_for(m->n_elem), kThreads, 0, s>>>(m->view<float>(), c.geo32.as<float4>());
+  FE_CHECK_LAUNCH();
+  c.geo_ready = true;
+}
+
+bool build_coarse_matrix(fe_mesh* m, cudaStream_t s) {
+  build_coarse(m, s);
+  Coarse& c = m->coarse;
+  if (c.csr_ready) return true;
+  const int64_t N4 = c.n_nodes, E = m->n_elem;
+  if (!c.csr_pattern) {
+    // block pattern: each element couples its 4 corners pairwise
+    std::vector<int32_t> conn4((size_t)E * 4);
+    FE_CUDA(cudaMemcpyAsync(conn4.data(), c.conn4.ptr, conn4.size() * 4, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> cnt((size_t)N4 + 1, 0);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < 4; ++a) cnt[(size_t)conn4[(size_t)(4 * e + a)] + 1] += 4;
+    for (int64_t v = 0; v < N4; ++v) cnt[(size_t)v + 1] += cnt[(size_t)v];
+    std::vector<int32_t> cand((size_t)cnt[(size_t)N4]);
+    {
+      std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+      for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a) {
+          const int32_t ra = conn4[(size_t)(4 * e + a)];
+          for (int b = 0; b < 4; ++b) cand[(size_t)fill[(size_t)ra]++] = conn4[(size_t)(4 * e + b)];
+        }
+    }
+    std::vector<int32_t> rowptr((size_t)N4 + 1, 0), cols;
+    cols.reserve((size_t)N4 * 16);
+    for (int64_t v = 0; v < N4; ++v) {
+      auto b0 = cand.begin() + cnt[(size_t)v], b1 = cand.begin() + cnt[(size_t)v + 1];
+      std::sort(b0, b1);
+      auto e1 = std::unique(b0, b1);
+      cols.insert(cols.end(), b0, e1);
+      FE_REQUIRE(cols.size() < (size_t)INT32_MAX, "coarse matrix too large for 32-bit block indices");
+      rowptr[(size_t)v + 1] = (int32_t)cols.size();
+    }
+    c.nnzb = (int64_t)cols.size();
+    c.rowptr.alloc(rowptr.size() * 4);
+    c.cols.alloc(cols.size() * 4);
+    FE_CUDA(cudaMemcpyAsync(c.rowptr.ptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaMemcpyAsync(c.cols.ptr, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    c.csr_pattern = true;
+  }
+  // the FP32 matrix stays, the FP64 accumulator is temporary: use the assembled
+  // form only where both fit in a quarter of the free memory
+  size_t free_b = 0, total_b = 0;
+  FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t need = (size_t)c.nnzb * 9 * (sizeof(float) + sizeof(double));
+  if (!c.vals32.ptr && need > free_b / 4) return false;
+  DevBuf v64, missing;
+  v64.alloc((size_t)c.nnzb * 9 * sizeof(double));
+  missing.alloc(sizeof(int));
+  if (!c.vals32.ptr) c.vals32.alloc((size_t)c.nnzb * 9 * sizeof(float));
+  FE_CUDA(cudaMemsetAsync(v64.ptr, 0, v64.bytes, s));
+  FE_CUDA(cudaMemsetAsync(missing.ptr, 0, sizeof(int), s));
+  assemble4_kernel<<<blocks_for(E), kThreads, 0, s>>>(m->view<double>(), c.conn4.as<int32_t>(), c.rowptr.as<int32_t>(),
+                                                       c.cols.as<int32_t>(), v64.as<double>(), missing.as<int>());
+  FE_CHECK_LAUNCH();
+  mask4_blocks_kernel<<<blocks_for(N4), kThreads, 0, s>>>(N4, c.rowptr.as<int32_t>(), c.cols.as<int32_t>(),
+                                                          c.nmask4.as<uint8_t>(), v64.as<double>(), c.vals32.as<float>());
+  FE_CHECK_LAUNCH();
+  int hmiss = 0;
+  FE_CUDA(cudaMemcpyAsync(&hmiss, missing.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  FE_REQUIRE(hmiss == 0, "coarse matrix assembly: block outside the pattern");
+  c.csr_ready = true;
+  return true;
+}
+
+void coarse_spmv(const fe_mesh* m, int R, const float* x4, float* y4, cudaStream_t s, const int* skip) {
+  const Coarse& c = m->coarse;
+  FE_REQUIRE(c.csr_ready, "coarse matrix not assembled");
+  spmv4_kernel<<<blocks_for(c.n_nodes * R), kThreads, 0, s>>>(c.n_nodes, R, c.rowptr.as<int32_t>(),
+                                                              c.cols.as<int32_t>(), c.vals32.as<float>(), x4, y4, skip);
+  FE_CHECK_LAUNCH();
+}
+
 template <typename T>
 static int case_group(int R) {
   return (sizeof(T) == 4 && R % 4 == 0) ? 4 : 1;
@@ -391,6 +619,7 @@ template <typename T>
 void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
   FE_REQUIRE(c.ready, "coarse level not built");
+  FE_REQUIRE(sizeof(T) == 8 || c.geo_ready, "coarse element data not built");
   const int64_t n4 = c.n_nodes * (int64_t)R * 3;
   zero4_kernel<T><<<std::min<unsigned>(blocks_for(n4), 152 * 16), kThreads, 0, s>>>(n4, y4, skip);
   FE_CHECK_LAUNCH();
@@ -398,14 +627,14 @@ void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, con
   const unsigned grid = blocks_for(m->n_elem * (R / W));
   if constexpr (sizeof(T) == 4) {
     if (W == 4) {
-      ebe4_kernel<T, 4><<<grid, kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(), c.nmask4.as<uint8_t>(),
-                                                  c.own4.as<uint8_t>(), x4, y4, skip);
+      ebe4_kernel<T, 4><<<grid, kThreads, 0, s>>>(m->view<T>(), c.geo32.as<float4>(), R, c.conn4.as<int32_t>(),
+                                                  c.nmask4.as<uint8_t>(), c.own4.as<uint8_t>(), x4, y4, skip);
       FE_CHECK_LAUNCH();
       return;
     }
   }
-  ebe4_kernel<T, 1><<<grid, kThreads, 0, s>>>(m->view<T>(), R, c.conn4.as<int32_t>(), c.nmask4.as<uint8_t>(),
-                                                c.own4.as<uint8_t>(), x4, y4, skip);
+  ebe4_kernel<T, 1><<<grid, kThreads, 0, s>>>(m->view<T>(), c.geo32.as<float4>(), R, c.conn4.as<int32_t>(),
+                                                c.nmask4.as<uint8_t>(), c.own4.as<uint8_t>(), x4, y4, skip);
   FE_CHECK_LAUNCH();
 }
 
@@ -489,7 +718,7 @@ extern "C" fe_status fe_ebe4_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtyp
     fe_mesh* m = coarse_args(mesh, R, dtype, x4, y4);
     fe::DeviceGuard dg(m->device);
     cudaStream_t s = (cudaStream_t)stream;
-    fe::build_coarse(m, s);
+    fe::build_coarse_geometry(m, s);
     if (dtype == FE_F64)
       fe::ebe4_apply<double>(m, R, (const double*)x4, (double*)y4, s);
     else
@@ -533,5 +762,15 @@ extern "C" fe_status fe_coarse_block_jacobi(const fe_mesh* mesh, double* binv4_d
     cudaStream_t s = (cudaStream_t)stream;
     fe::build_coarse_jacobi(m, s);
     FE_CUDA(cudaMemcpyAsync(binv4_dev, m->coarse.binv64.ptr, m->coarse.binv64.bytes, cudaMemcpyDeviceToDevice, s));
+  });
+}
+
+extern "C" fe_status fe_coarse_apply(const fe_mesh* mesh, int32_t R, const float* x4, float* y4, void* stream) {
+  return fe::guarded([&] {
+    fe_mesh* m = coarse_args(mesh, R, FE_F32, x4, y4);
+    fe::DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    FE_REQUIRE(fe::build_coarse_matrix(m, s), "not enough free device memory for the assembled coarse matrix");
+    fe::coarse_spmv(m, R, x4, y4, s);
   });
 }

@@ -143,6 +143,13 @@ struct Coarse {
   DevBuf adj_ptr, adj;      // int32 [N4 + 1], [2 * edge nodes]: edge nodes ending at each coarse node
   bool jacobi_ready = false;
   DevBuf binv64, binv32;    // [N4][9] inverse diagonal blocks of K1_bc
+  bool geo_ready = false;
+  DevBuf geo32;             // float [E][16]: grad L_0..3, lam V, mu V, pad (FP32 TET4 products)
+  // assembled K1_bc in 3x3 block CSR (built on first use, per material state)
+  bool csr_pattern = false, csr_ready = false;
+  int64_t nnzb = 0;
+  DevBuf rowptr, cols;      // int32 [N4 + 1], [nnzb] (columns sorted per row)
+  DevBuf vals32;            // float [nnzb][9]
 };
 
 struct SolverWork;  // defined in fe_solver.cu
@@ -220,6 +227,9 @@ void free_solver_work(fe_mesh* m);
 // Coarse level (fe_coarse.cu)
 void build_coarse(fe_mesh* m, cudaStream_t s);
 void build_coarse_jacobi(fe_mesh* m, cudaStream_t s);
+void build_coarse_geometry(fe_mesh* m, cudaStream_t s);
+bool build_coarse_matrix(fe_mesh* m, cudaStream_t s);  // false: not enough device memory
+void coarse_spmv(const fe_mesh* m, int R, const float* x4, float* y4, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip = nullptr);
 template <typename T>

@@ -813,6 +813,7 @@ struct Solve {
   size_t sm;  // shared bytes of reducing vector kernels
   int64_t N1 = 0;  // level-1 nodes (0: no coarse level)
   VGeom g1;
+  bool assembled1 = false;  // level-1 operator: assembled block CSR, else element by element
   cudaStream_t s;
   const double* f;
   double* u;
@@ -897,7 +898,9 @@ struct Level {
 };
 
 static void level_apply(Solve& S, const Level& L, const float* x, float* y, const int* skip) {
-  if (L.coarse)
+  if (L.coarse && S.assembled1)
+    coarse_spmv(S.m, S.R, x, y, S.s, skip);
+  else if (L.coarse)
     ebe4_apply<float>(S.m, S.R, x, y, S.s, skip);
   else
     ebe_apply<float>(S.m, S.R, x, y, S.s, skip);
@@ -1044,6 +1047,9 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   const bool pcg = o.solver == FE_SOLVER_PCG64;
   if (o.solver == FE_SOLVER_FCG_MG) {
     build_coarse_jacobi(m, s);
+    S.assembled1 = o.coarse_op != 2 && build_coarse_matrix(m, s);
+    FE_REQUIRE(o.coarse_op != 1 || S.assembled1, "not enough free device memory for the assembled coarse matrix");
+    if (!S.assembled1) build_coarse_geometry(m, s);
     S.N1 = m->coarse.n_nodes;
     S.g1 = vgeom(S.N1, R, sms);
     const size_t v1 = (size_t)S.N1 * R * 3 * sizeof(float);
@@ -1223,6 +1229,7 @@ static void check_opts(const fe_solve_opts& o) {
   if (o.solver == FE_SOLVER_FCG_MG) {
     FE_REQUIRE(o.n_inner1 >= 0 && o.n_inner1 <= 100000, "n_inner1 out of range");
     FE_REQUIRE(o.eps_inner1 >= 0.0, "eps_inner1 must be >= 0");
+    FE_REQUIRE(o.coarse_op >= 0 && o.coarse_op <= 2, "coarse_op must be 0, 1 or 2");
   }
 }
 

@@ -20,6 +20,7 @@ FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT = 
 FE_F64, FE_F32 = 0, 1
 FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED, FE_SOLVER_FCG_MG = 0, 1, 2
 SOLVERS = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED, "fcg_mg": FE_SOLVER_FCG_MG}
+COARSE_OPS = {"auto": 0, "assembled": 1, "ebe": 2}
 EBE_DIRECT, EBE_TILED = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
@@ -30,7 +31,7 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
             "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
-            "fe_coarse_prolong", "fe_coarse_block_jacobi"]
+            "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply"]
 
 
 class FeError(RuntimeError):
@@ -43,7 +44,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("n_inner", ctypes.c_int32), ("eps_inner", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32),
-                ("n_inner1", ctypes.c_int32), ("eps_inner1", ctypes.c_double)]
+                ("n_inner1", ctypes.c_int32), ("eps_inner1", ctypes.c_double), ("coarse_op", ctypes.c_int32),
+                ("pad1", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -90,10 +92,11 @@ def load(path: Optional[str] = None):
     lib.fe_coarse_restrict.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     lib.fe_coarse_prolong.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     lib.fe_coarse_block_jacobi.argtypes = [_vp, _vp, _vp]
+    lib.fe_coarse_apply.argtypes = [_vp, _i32, _vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
-                 "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi"):
+                 "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,7 +230,8 @@ class Mesh:
     # ---- solvers --------------------------------------------------------
     def solve(self, f, u0=None, solver: str = "fcg_mixed", tol: float = 1e-8, max_outer: int = 20000,
               n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
-              check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, raise_on_fail: bool = True):
+              check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
+              raise_on_fail: bool = True):
         """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status)."""
         torch = _torch()
         R = int(f.shape[1])
@@ -240,6 +244,7 @@ class Mesh:
         o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
         o.use_graph, o.literal_beta, o.check_every = int(bool(use_graph)), int(bool(literal_beta)), int(check_every)
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
+        o.coarse_op = COARSE_OPS[coarse_op]
         stats = (SolveStats * R)()
         st = load().fe_pcg_solve(self._h, R, fp, up, ctypes.byref(o), stats, self._stream())
         out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, relres=s.relres,
@@ -250,7 +255,8 @@ class Mesh:
 
     def solve_many(self, f_cases, R_slots: int = 0, solver: str = "fcg_mixed", tol: float = 1e-8,
                    max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
-                   n_inner1: int = 300, eps_inner1: float = 0.05, raise_on_fail: bool = True):
+                   n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
+                   raise_on_fail: bool = True):
         """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
         in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
         torch = _torch()
@@ -263,6 +269,7 @@ class Mesh:
         o.tol, o.max_outer, o.n_inner, o.eps_inner = float(tol), int(max_outer), int(n_inner), float(eps_inner)
         o.use_graph = int(bool(use_graph))
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
+        o.coarse_op = COARSE_OPS[coarse_op]
         stats = (SolveStats * n)()
         r_used = _i32()
         st = load().fe_solve_many(self._h, n, fp, ctypes.c_void_p(u.data_ptr()), int(R_slots), ctypes.byref(o),
@@ -313,6 +320,18 @@ class Mesh:
         """y4 = K1_bc x4 on the TET4 coarse mesh, x4 [N4, R, 3]."""
         n4 = self._n4()
         return self._coarse_vec("fe_ebe4_apply", x4, n4, n4)
+
+    def coarse_apply(self, x4):
+        """y4 = K1_bc x4 with the assembled coarse matrix (FP32), x4 [N4, R, 3]."""
+        torch = _torch()
+        n4 = self._n4()
+        if x4.dim() != 3 or x4.shape[0] != n4 or x4.shape[2] != 3:
+            raise ValueError(f"x4 must be [{n4}, R, 3]")
+        xp = _dev_ptr(x4, torch.float32, name="x4")
+        y = torch.empty_like(x4)
+        _check(load().fe_coarse_apply(self._h, int(x4.shape[1]), xp, ctypes.c_void_p(y.data_ptr()), self._stream()),
+               "fe_coarse_apply")
+        return y
 
     def coarse_restrict(self, r10):
         """r4 = P (P1^T r10): [N, R, 3] -> [N4, R, 3]."""

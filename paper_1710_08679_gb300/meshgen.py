@@ -267,15 +267,37 @@ def interface_nodes(mesh: Mesh, iface: Interface) -> Tuple[np.ndarray, np.ndarra
     return on, hw
 
 
+def bspline3(t: np.ndarray) -> np.ndarray:
+    """Centred cubic B-spline of unit knot spacing (support [-2, 2], B(0) = 2/3)."""
+    a = np.abs(np.asarray(t, dtype=np.float64))
+    return np.where(a < 1.0, 2.0 / 3.0 - a * a + 0.5 * a ** 3,
+                    np.where(a < 2.0, (2.0 - a) ** 3 / 6.0, 0.0))
+
+
 def slip_patch(mesh: Mesh, iface: Interface, on_iface: np.ndarray, hw: np.ndarray,
-               center: Tuple[float, float], size: float, direction: str) -> SlipCase:
+               center: Tuple[float, float], size: float, direction: str,
+               profile: str = "uniform") -> SlipCase:
+    """Unit slip on the interface nodes within a size x size patch (fault-plane
+    coordinates). profile "uniform": slip 1 on the whole patch; "bspline": slip
+    B(4 s / size) B(4 d / size) / B(0)^2 in the along-strike and down-dip offsets
+    (s, d) from the centre, a tensor cubic B-spline that is 1 at the centre and
+    vanishes smoothly at the patch edge (the paper's unit B-spline slips, Sec. 5)."""
     pc = iface.plane_coords(mesh.coords)
     half = 0.5 * size
     sel = on_iface & (np.abs(pc[:, 0] - center[0]) <= half + 1e-9) & \
         (np.abs(pc[:, 1] - center[1]) <= half + 1e-9)
     vec = iface.dip_vector() if direction == "dip" else iface.strike_vector()
     slip = np.zeros((mesh.n_nodes, 3))
-    slip[sel] = vec
+    if profile == "uniform":
+        slip[sel] = vec
+    elif profile == "bspline":
+        amp = bspline3(4.0 * (pc[sel, 0] - center[0]) / size) * bspline3(4.0 * (pc[sel, 1] - center[1]) / size)
+        amp /= (2.0 / 3.0) ** 2
+        slip[sel] = amp[:, None] * vec[None, :]
+        sel = sel.copy()
+        sel[np.nonzero(sel)[0][amp == 0.0]] = False
+    else:
+        raise ValueError(f"unknown slip profile {profile!r}")
     touch = np.zeros(mesh.n_elem, dtype=bool)
     touch |= np.any(sel[mesh.conn], axis=1)
     elems = np.nonzero(touch & hw)[0]
@@ -402,6 +424,33 @@ def crust_block(shape=(70, 70, 35), h: float = 1000.0, jitter: float = 0.15, see
     return m, iface
 
 
+# The paper's two-layer measurement model (its table of material properties):
+# (Vp m/s, Vs m/s, density kg/m^3) of layer 1 (top) and layer 2.
+PAPER_LAYERS = ((1600.0, 400.0, 1850.0), (5800.0, 3000.0, 2700.0))
+
+
+def elastic_from_velocities(vp: float, vs: float, rho: float) -> Tuple[float, float]:
+    """Isotropic (E, nu) of a medium with P and S wave speeds vp, vs and density
+    rho: mu = rho vs^2, lambda = rho (vp^2 - 2 vs^2)."""
+    mu = rho * vs * vs
+    lam = rho * (vp * vp - 2.0 * vs * vs)
+    return mu * (3.0 * lam + 2.0 * mu) / (lam + mu), lam / (2.0 * (lam + mu))
+
+
+def two_layer_block(shape=(70, 70, 35), h: float = 1000.0, soft_thickness: float = 5000.0,
+                    jitter: float = 0.15, seed: int = 4) -> Tuple[Mesh, Interface]:
+    """The paper's two-layer model on a crust block: layer 1 (Vp 1,600 m/s, Vs 400
+    m/s, 1,850 kg/m^3: E = 0.87 GPa, nu = 0.467) in the top `soft_thickness`, layer
+    2 (5,800 / 3,000 / 2,700: E = 64 GPa, nu = 0.317) below, split by element
+    centroid; the dipping interface of the crust blocks carries the slip sources."""
+    lengths = tuple(float(v) * h for v in shape)
+    m = box_mesh(shape, lengths, jitter=jitter, seed=seed, name=f"two_layer_{shape[0]}x{shape[1]}x{shape[2]}")
+    iface = crust_interface(lengths)
+    set_two_layers(m, lengths[2] - soft_thickness, upper=elastic_from_velocities(*PAPER_LAYERS[0]),
+                   lower=elastic_from_velocities(*PAPER_LAYERS[1]))
+    return m, iface
+
+
 def random_vectors(n_nodes: int, R: int, seed: int) -> np.ndarray:
     """x ~ N(0,1), float64 [N, R, 3] (PCG64)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -409,7 +458,7 @@ def random_vectors(n_nodes: int, R: int, seed: int) -> np.ndarray:
 
 
 def patch_grid_cases(mesh: Mesh, iface: Interface, n_along: int = 4, spacing: float = 4000.0,
-                     size: float = 2000.0, direction: str = "dip") -> List[SlipCase]:
+                     size: float = 2000.0, direction: str = "dip", profile: str = "uniform") -> List[SlipCase]:
     """n_along x n_along patches centred in the box, `spacing` apart along strike
     and along dip."""
     on, hw = interface_nodes(mesh, iface)
@@ -424,7 +473,7 @@ def patch_grid_cases(mesh: Mesh, iface: Interface, n_along: int = 4, spacing: fl
     cases = []
     for a in offs:
         for b in offs:
-            cases.append(slip_patch(mesh, iface, on, hw, (mid_y + a, mid_dd + b), size, direction))
+            cases.append(slip_patch(mesh, iface, on, hw, (mid_y + a, mid_dd + b), size, direction, profile))
     return cases
 
 

@@ -67,6 +67,17 @@ def test_ebe4_matches_assembled_tet4_operator(meshes, name, R, dtype):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("name", ["box8", "crust9x5x4"])
+@pytest.mark.parametrize("R", [1, 3, 16])
+def test_assembled_coarse_operator_matches_oracle(meshes, name, R):
+    m, cm, M = meshes[name]
+    K1 = oracle.assemble4(cm)
+    x = mg.random_vectors(cm.vertex.size, R, seed=310 + R).astype(np.float32).astype(np.float64)
+    y = M.coarse_apply(cuda(x, torch.float32)).double().cpu().numpy()
+    assert rel_l2(y, oracle.spmv(K1, x)) <= TOL32
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["box8", "crust9x5x4"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("R", [5, 8])
 def test_transfers_match_oracle(meshes, name, dtype, R):
@@ -115,6 +126,13 @@ def test_galerkin_identity_at_full_size():
     rhs = M.ebe4(X4).cpu().numpy()
     mask = free4[:, None, :].repeat(2, 1) == 1
     assert rel_l2(lhs[mask], rhs[mask]) <= 1e-11
+    # the assembled FP32 operator and the FP32 element-by-element product agree
+    # with the FP64 product
+    x32 = torch.from_numpy(x4.astype(np.float32)).cuda()
+    y_asm = M.coarse_apply(x32).double().cpu().numpy()
+    y_ebe = M.ebe4(x32).double().cpu().numpy()
+    y64 = M.ebe4(x32.double()).cpu().numpy()
+    assert rel_l2(y_asm, y64) <= TOL32 and rel_l2(y_ebe, y64) <= TOL32
     # sampled rows against element matrices of the oracle
     rng = np.random.default_rng(3)
     conn4 = np.searchsorted(vertex, m.conn[:, :4])
@@ -142,9 +160,10 @@ def box8_solve(meshes):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_fcg_mg_plain_box(box8_solve, use_graph):
+@pytest.mark.parametrize("coarse_op", ["assembled", "ebe"])
+def test_fcg_mg_plain_box(box8_solve, use_graph, coarse_op):
     m, cm, M, K, f = box8_solve
-    u, stats, st = M.solve(cuda(f), solver="fcg_mg", tol=1e-8, use_graph=use_graph)
+    u, stats, st = M.solve(cuda(f), solver="fcg_mg", tol=1e-8, use_graph=use_graph, coarse_op=coarse_op)
     assert st == 0
     assert stats[0]["relres"] <= 1e-8
     ud = oracle.direct_solve(K, f)
@@ -228,6 +247,7 @@ def test_set_log_young_rebuilds_coarse_preconditioner(meshes):
     cm = oracle.coarse_mesh(m)
     M = fe.Mesh.from_mesh(m)
     before = M.coarse_block_jacobi().cpu().numpy()
+    M.coarse_apply(cuda(np.zeros((cm.vertex.size, 1, 3)), torch.float32))   # assembled before the change
     le = np.log(m.young) + 0.2 * np.random.default_rng(6).standard_normal(m.n_elem)
     M.set_log_young(cuda(le))
     after = M.coarse_block_jacobi().cpu().numpy()
@@ -235,5 +255,9 @@ def test_set_log_young_rebuilds_coarse_preconditioner(meshes):
     assert block_rel_err(after, ref) <= TOL64
     assert block_rel_err(after, before) > 1e-3
     x = mg.random_vectors(cm.vertex.size, 2, seed=8)
+    K1 = oracle.assemble4(cm, young=np.exp(le))
     y = M.ebe4(cuda(x)).cpu().numpy()
-    assert rel_l2(y, oracle.spmv(oracle.assemble4(cm, young=np.exp(le)), x)) <= TOL64
+    assert rel_l2(y, oracle.spmv(K1, x)) <= TOL64
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = M.coarse_apply(cuda(x32, torch.float32)).double().cpu().numpy()
+    assert rel_l2(y32, oracle.spmv(K1, x32)) <= TOL32
