@@ -86,6 +86,16 @@ def configure(lib):
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                       _u8p, ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _u8p, _i32p, ctypes.c_int,
                                       ctypes.c_double, _i32p, _i32p, _i32p, _f64p]
+        lib.oracle_aggregate.argtypes = [ctypes.c_int64, _i64p, _i32p, _i32p]
+        lib.oracle_aggregate.restype = ctypes.c_int64
+        lib.oracle_galerkin_agg.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _u8p, _i32p, ctypes.c_int64,
+                                            _i64p, _i32p, _f64p, _u8p]
+        lib.oracle_galerkin_agg.restype = ctypes.c_int64
+        lib.oracle_fcg_ml.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int, _f64p, _f64p,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      _u8p, ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _u8p, _i32p, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _i32p,
+                                      ctypes.c_int, ctypes.c_double, _i32p, _i32p, _i32p, _i32p, _f64p]
     return lib
 
 
@@ -384,3 +394,75 @@ def fcg_mg(K: Assembled, f: np.ndarray, coarse: Coarse = None, K1: Assembled = N
     if rc != 0:
         raise RuntimeError("fcg_mg failed (%d)" % rc)
     return u, outer, inner, inner1, rel
+
+
+# ---------------------------------------------------------------------------
+# level 2: aggregation coarsening of the TET4 level
+# ---------------------------------------------------------------------------
+
+def aggregate(K1: Assembled) -> np.ndarray:
+    """Plain aggregation of K1's node graph (two passes in node order, see
+    oracle_aggregate): int32 aggregate id per coarse node."""
+    lib = _load()
+    agg = np.empty(K1.n_nodes, dtype=np.int32)
+    n = lib.oracle_aggregate(K1.n_nodes, _p(K1.rowptr, _i64p), _p(K1.col, _i32p), _p(agg, _i32p))
+    if n < 0:
+        raise RuntimeError("aggregation failed (%d)" % n)
+    return agg
+
+
+def galerkin_agg(K1: Assembled, free4: np.ndarray, agg: np.ndarray):
+    """A2 = P2^T K1_bc P2 on the free aggregate DOFs, identity on the others:
+    (Assembled A2, free2 [NA, 3])."""
+    lib = _load()
+    NA = int(agg.max()) + 1
+    free4 = _c(free4, np.uint8)
+    agg = _c(agg, np.int32)
+    cap = int(K1.rowptr[-1])
+    rowptr2 = np.zeros(NA + 1, dtype=np.int64)
+    col2 = np.zeros(cap, dtype=np.int32)
+    vals2 = np.zeros((cap, 3, 3))
+    free2 = np.zeros((NA, 3), dtype=np.uint8)
+    nnz = lib.oracle_galerkin_agg(K1.n_nodes, _p(K1.rowptr, _i64p), _p(K1.col, _i32p), _p(K1.vals, _f64p),
+                                  _p(free4, _u8p), _p(agg, _i32p), NA, _p(rowptr2, _i64p), _p(col2, _i32p),
+                                  _p(vals2, _f64p), _p(free2, _u8p))
+    if nnz < 0:
+        raise RuntimeError("galerkin_agg failed (%d)" % nnz)
+    return Assembled(n_nodes=NA, rowptr=rowptr2, col=col2[:nnz].copy(), vals=vals2[:nnz].copy()), free2
+
+
+def fcg_ml(K: Assembled, f: np.ndarray, coarse: Coarse, free, K1: Assembled = None, levels: int = 3, u0=None,
+           tol: float = 1e-8, max_outer: int = 10000, n_inner: int = 30, eps_inner: float = 0.1,
+           n_inner1: int = 300, eps_inner1: float = 0.05, n_inner2: int = 3000, eps_inner2: float = 0.025,
+           literal_beta: bool = False):
+    """Algorithm 1 with inner loops at levels 2 (aggregation of the TET4 level), 1
+    (TET4) and 0: (u, outer, inner0_total, inner1_total, inner2_total, relres)."""
+    lib = _load()
+    f = _c(f, np.float64)
+    R = f.shape[1]
+    u = np.zeros_like(f) if u0 is None else _c(u0, np.float64).copy()
+    Minv = block_jacobi(K)
+    if K1 is None:
+        K1 = assemble4(coarse)
+    Minv1 = block_jacobi(K1)
+    ends = _c(coarse.ends, np.int32)
+    free4 = _c(coarse.free, np.uint8)
+    free10 = _c(free, np.uint8)
+    counts = [np.zeros(R, dtype=np.int32) for _ in range(4)]
+    rel = np.zeros(R)
+    if levels >= 3:
+        agg = aggregate(K1)
+        A2, _ = galerkin_agg(K1, free4, agg)
+        Minv2 = block_jacobi(A2)
+        args2 = (A2.n_nodes, _p(A2.rowptr, _i64p), _p(A2.col, _i32p), _p(A2.vals, _f64p), _p(Minv2, _f64p),
+                 _p(agg, _i32p), int(n_inner2), float(eps_inner2))
+    else:
+        args2 = (0, None, None, None, None, None, 0, 0.0)
+    rc = lib.oracle_fcg_ml(K.n_nodes, _p(K.rowptr, _i64p), _p(K.col, _i32p), _p(K.vals, _f64p), _p(Minv, _f64p), R,
+                           _p(f, _f64p), _p(u, _f64p), float(tol), int(max_outer), int(n_inner), float(eps_inner),
+                           int(bool(literal_beta)), _p(free10, _u8p), K1.n_nodes, _p(K1.rowptr, _i64p),
+                           _p(K1.col, _i32p), _p(K1.vals, _f64p), _p(Minv1, _f64p), _p(free4, _u8p), _p(ends, _i32p),
+                           int(n_inner1), float(eps_inner1), *args2, *[_p(c, _i32p) for c in counts], _p(rel, _f64p))
+    if rc != 0:
+        raise RuntimeError("fcg_ml failed (%d)" % rc)
+    return (u, *counts, rel)

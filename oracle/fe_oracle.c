@@ -21,7 +21,9 @@
  *   - 3x3 block Jacobi M = diag[K_bc] (Algorithm 1(a), its set-up);
  *   - preconditioned CG with 3x3 block Jacobi (the PCGE baseline of Sec. 4);
  *   - the flexible (adaptive) CG of Algorithm 1(a) with the FP32 inner PCG of
- *     Algorithm 1(b) at level 0, for R cases at once;
+ *     Algorithm 1(b) at level 0, and optionally at level 1 (the TET4 mesh of the
+ *     same corners) and level 2 (an aggregation coarsening of level 1), for R
+ *     cases at once;
  *   - the adjoint element sensitivity g_e = -sum_r lambda_r^T (dK_bc/dm_e) u_r
  *     for m_e = log E_e (no counterpart in the paper).
  *
@@ -666,10 +668,152 @@ static int inner_pcg_f32(int64_t N, const int64_t* rowptr, const int32_t* col, c
   return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* level 2: algebraic coarsening of the TET4 level (Sec. 2)                   */
+/* ------------------------------------------------------------------------- */
+
+/* Plain aggregation of the nodes of a block matrix's graph (neighbours: the
+ * other columns of a node's block row), two passes in node order:
+ *   pass 1: a node that is not aggregated and none of whose neighbours is
+ *           aggregated starts a new aggregate made of itself and all its
+ *           neighbours;
+ *   pass 2: each node still without aggregate joins the pass-1 aggregate of its
+ *           lowest-numbered neighbour that has one (every such node has one: it
+ *           was skipped in pass 1 because a neighbour was taken).
+ * Writes agg[N] and returns the number of aggregates. */
+int64_t oracle_aggregate(int64_t N, const int64_t* rowptr, const int32_t* col, int32_t* agg) {
+  for (int64_t n = 0; n < N; ++n) agg[n] = -1;
+  int64_t count = 0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (agg[n] >= 0) continue;
+    int all_free = 1;
+    for (int64_t q = rowptr[n]; q < rowptr[n + 1]; ++q)
+      if (col[q] != n && agg[col[q]] >= 0) { all_free = 0; break; }
+    if (!all_free) continue;
+    agg[n] = (int32_t)count;
+    for (int64_t q = rowptr[n]; q < rowptr[n + 1]; ++q) agg[col[q]] = (int32_t)count;
+    ++count;
+  }
+  int32_t* first = malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  if (!first) return -2;
+  memcpy(first, agg, sizeof(int32_t) * (size_t)N);
+  for (int64_t n = 0; n < N; ++n) {
+    if (first[n] >= 0) continue;
+    int32_t best = -1;
+    for (int64_t q = rowptr[n]; q < rowptr[n + 1]; ++q) {
+      const int32_t j = col[q];
+      if (j != n && first[j] >= 0 && (best < 0 || j < best)) best = j;
+    }
+    if (best < 0) { free(first); return -1; }
+    agg[n] = first[best];
+  }
+  free(first);
+  return count;
+}
+
+/* Galerkin coarse matrix of the aggregation: with P2 the piecewise-constant
+ * prolongation (aggregate value copied to each member node, component by
+ * component, on the member's free DOFs only),
+ *   A2 = P2^T K1_bc P2 on the free aggregate DOFs (those with a free member),
+ *   identity on the others.
+ * Block-row a of K1 adds its blocks, restricted to free (row, column) DOFs, into
+ * block-row agg[a] at block-column agg[b]. Outputs A2 in block CSR (columns
+ * increasing within a row; capacity rowptr[N] blocks, always enough) and
+ * free2[NA][3]. Returns the number of blocks of A2. */
+int64_t oracle_galerkin_agg(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals,
+                            const uint8_t* free_mask, const int32_t* agg, int64_t NA, int64_t* rowptr2,
+                            int32_t* col2, double* vals2, uint8_t* free2) {
+  int64_t* mstart = calloc((size_t)NA + 1, sizeof(int64_t));
+  int64_t* members = malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  int64_t* pos = malloc(sizeof(int64_t) * (size_t)(NA > 0 ? NA : 1));
+  if (!mstart || !members || !pos) return -2;
+  for (int64_t n = 0; n < N; ++n) mstart[agg[n] + 1]++;
+  for (int64_t A = 0; A < NA; ++A) mstart[A + 1] += mstart[A];
+  {
+    int64_t* fill = malloc(sizeof(int64_t) * (size_t)(NA > 0 ? NA : 1));
+    if (!fill) return -2;
+    memcpy(fill, mstart, sizeof(int64_t) * (size_t)NA);
+    for (int64_t n = 0; n < N; ++n) members[fill[agg[n]]++] = n;
+    free(fill);
+  }
+  for (int64_t A = 0; A < NA; ++A) pos[A] = -1;
+  int64_t nnz = 0;
+  rowptr2[0] = 0;
+  for (int64_t A = 0; A < NA; ++A) {
+    const int64_t row0 = nnz;
+    for (int i = 0; i < 3; ++i) free2[3 * A + i] = 0;
+    for (int64_t k = mstart[A]; k < mstart[A + 1]; ++k) {
+      const int64_t a = members[k];
+      for (int i = 0; i < 3; ++i) free2[3 * A + i] |= free_mask[3 * a + i];
+      for (int64_t q = rowptr[a]; q < rowptr[a + 1]; ++q) {
+        const int64_t b = col[q];
+        const int32_t B = agg[b];
+        if (pos[B] < 0) {
+          pos[B] = nnz;
+          col2[nnz] = B;
+          for (int t = 0; t < 9; ++t) vals2[9 * nnz + t] = 0.0;
+          ++nnz;
+        }
+        double* dst = vals2 + 9 * pos[B];
+        const double* src = vals + 9 * q;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            if (free_mask[3 * a + i] && free_mask[3 * b + j]) dst[3 * i + j] += src[3 * i + j];
+      }
+    }
+    for (int64_t t = row0; t < nnz; ++t) {
+      if (col2[t] == A)
+        for (int i = 0; i < 3; ++i)
+          if (!free2[3 * A + i]) vals2[9 * t + 4 * i] = 1.0;
+      pos[col2[t]] = -1;
+    }
+    /* columns in increasing order within the row (insertion sort, rows are short) */
+    for (int64_t t = row0 + 1; t < nnz; ++t) {
+      const int32_t c = col2[t];
+      double v[9];
+      for (int k = 0; k < 9; ++k) v[k] = vals2[9 * t + k];
+      int64_t w = t;
+      while (w > row0 && col2[w - 1] > c) {
+        col2[w] = col2[w - 1];
+        for (int k = 0; k < 9; ++k) vals2[9 * w + k] = vals2[9 * (w - 1) + k];
+        --w;
+      }
+      col2[w] = c;
+      for (int k = 0; k < 9; ++k) vals2[9 * w + k] = v[k];
+    }
+    rowptr2[A + 1] = nnz;
+  }
+  free(mstart); free(members); free(pos);
+  return nnz;
+}
+
+/* r2 = P2^T r1 (free fine DOFs summed into their aggregate) */
+static void restrict_agg_f32(int64_t N, int64_t NA, int R, const int32_t* agg, const uint8_t* free_mask,
+                             const float* r1, float* r2) {
+  memset(r2, 0, sizeof(float) * 3 * (size_t)NA * R);
+  for (int64_t n = 0; n < N; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i)
+        if (free_mask[3 * n + i]) r2[3 * ((int64_t)agg[n] * R + r) + i] += r1[3 * (n * R + r) + i];
+}
+
+/* u1 = P2 u2 (aggregate value on each member's free DOFs) */
+static void prolong_agg_f32(int64_t N, int R, const int32_t* agg, const uint8_t* free_mask, const float* u2,
+                            float* u1) {
+  for (int64_t n = 0; n < N; ++n)
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < 3; ++i)
+        u1[3 * (n * R + r) + i] = free_mask[3 * n + i] ? u2[3 * ((int64_t)agg[n] * R + r) + i] : 0.0f;
+}
+
 /* Outer loop (FP64), per case r while ||r||/||f|| > tol (per-case masking):
  *   rbar = (float) r; ubar = Mbar^-1 rbar
  *   with the TET4 level (N4 > 0), inner loop level 1:
  *     rbar1 = P1^T rbar; ubar1 = P1^T ubar
+ *     with the aggregation level (N2 > 0), inner loop level 2:
+ *       rbar2 = P2^T rbar1; ubar2 = P2^T ubar1
+ *       inner loop (b) on Abar2 ubar2 = rbar2 with eps_inner2, n_inner2
+ *       ubar1 = P2 ubar2
  *     inner loop (b) on Kbar1 ubar1 = rbar1 with eps_inner1, n_inner1
  *     ubar = P1 ubar1
  *   inner loop level 0: (b) on Kbar ubar = rbar with eps_inner, n_inner
@@ -683,17 +827,20 @@ static int inner_pcg_f32(int64_t N, const int64_t* rowptr, const int32_t* col, c
  * has converged are frozen (they skip the inner loops and do not count in their
  * max rule). outer[r], inner_total[r] (level 0 steps), inner1_total[r] (level 1
  * steps), relres[r] (true residual) are written. */
-int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
+int oracle_fcg_ml(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
                   int R, const double* f, double* u, double tol, int max_outer, int n_inner, double eps_inner,
                   int literal_beta, const uint8_t* free_mask, int64_t N4, const int64_t* rowptr4,
                   const int32_t* col4, const double* vals4, const double* Minv4, const uint8_t* free4,
-                  const int32_t* ends, int n_inner1, double eps_inner1,
-                  int32_t* outer, int32_t* inner_total, int32_t* inner1_total, double* relres) {
+                  const int32_t* ends, int n_inner1, double eps_inner1, int64_t N2, const int64_t* rowptr2,
+                  const int32_t* col2, const double* vals2, const double* Minv2, const int32_t* agg,
+                  int n_inner2, double eps_inner2, int32_t* outer, int32_t* inner_total, int32_t* inner1_total,
+                  int32_t* inner2_total, double* relres) {
   size_t nv = (size_t)N * R * 3, nv4 = (size_t)(N4 > 0 ? N4 : 1) * R * 3;
   int64_t nnzb = rowptr[N];
   float* vals32 = malloc(sizeof(float) * 9 * (size_t)nnzb);
   float* Minv32 = malloc(sizeof(float) * 9 * (size_t)N);
   float *vals4_32 = NULL, *Minv4_32 = NULL, *rb1 = NULL, *ub1 = NULL;
+  float *vals2_32 = NULL, *Minv2_32 = NULL, *rb2 = NULL, *ub2 = NULL;
   double *r = malloc(nv * 8), *z = malloc(nv * 8), *p = malloc(nv * 8), *q = malloc(nv * 8);
   float *rb = malloc(nv * 4), *ub = malloc(nv * 4);
   double *fn = malloc(R * 8), *rn = malloc(R * 8), *rho = malloc(R * 8), *gam = malloc(R * 8),
@@ -713,13 +860,24 @@ int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const do
     for (int64_t k = 0; k < 9 * rowptr4[N4]; ++k) vals4_32[k] = (float)vals4[k];
     for (int64_t k = 0; k < 9 * N4; ++k) Minv4_32[k] = (float)Minv4[k];
   }
+  if (N4 > 0 && N2 > 0) {
+    const size_t nv2 = (size_t)N2 * R * 3;
+    vals2_32 = malloc(sizeof(float) * 9 * (size_t)rowptr2[N2]);
+    Minv2_32 = malloc(sizeof(float) * 9 * (size_t)N2);
+    rb2 = malloc(nv2 * 4);
+    ub2 = malloc(nv2 * 4);
+    if (!vals2_32 || !Minv2_32 || !rb2 || !ub2) return -2;
+    for (int64_t k = 0; k < 9 * rowptr2[N2]; ++k) vals2_32[k] = (float)vals2[k];
+    for (int64_t k = 0; k < 9 * N2; ++k) Minv2_32[k] = (float)Minv2[k];
+  }
 
   oracle_spmv(N, rowptr, col, vals, R, u, q);            /* r = f - K u */
   for (size_t k = 0; k < nv; ++k) r[k] = f[k] - q[k];
   memset(p, 0, nv * 8);
   dots(N, R, f, f, fn);
   for (int c = 0; c < R; ++c) {
-    outer[c] = 0; inner_total[c] = 0; if (inner1_total) inner1_total[c] = 0; active[c] = fn[c] > 0.0;
+    outer[c] = 0; inner_total[c] = 0; if (inner1_total) inner1_total[c] = 0; if (inner2_total) inner2_total[c] = 0;
+    active[c] = fn[c] > 0.0;
   }
   int rc = 0;
   for (int it = 1; it <= max_outer; ++it) {
@@ -739,6 +897,14 @@ int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const do
       restrict_f32(N, N4, R, ends, ub, ub1);
       mask_f32(N4, R, free4, rb1);
       mask_f32(N4, R, free4, ub1);
+      if (N2 > 0) {
+        restrict_agg_f32(N4, N2, R, agg, free4, rb1, rb2);
+        restrict_agg_f32(N4, N2, R, agg, free4, ub1, ub2);
+        rc = inner_pcg_f32(N2, rowptr2, col2, vals2_32, Minv2_32, R, rb2, ub2, n_inner2, eps_inner2, active,
+                           inner2_total);
+        if (rc) break;
+        prolong_agg_f32(N4, R, agg, free4, ub2, ub1);
+      }
       rc = inner_pcg_f32(N4, rowptr4, col4, vals4_32, Minv4_32, R, rb1, ub1, n_inner1, eps_inner1, active,
                          inner1_total);
       if (rc) break;
@@ -782,10 +948,23 @@ int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const do
   for (size_t k = 0; k < nv; ++k) r[k] = f[k] - q[k];
   dots(N, R, r, r, rn);
   for (int c = 0; c < R; ++c) relres[c] = fn[c] > 0.0 ? sqrt(rn[c] / fn[c]) : 0.0;
+  free(vals2_32); free(Minv2_32); free(rb2); free(ub2);
   free(vals32); free(Minv32); free(vals4_32); free(Minv4_32); free(rb1); free(ub1); free(r); free(z); free(p);
   free(q); free(rb); free(ub); free(fn); free(rn); free(rho); free(gam); free(zq); free(pq_prev); free(rho_prev);
   free(bet); free(active);
   return rc;
+}
+
+/* Levels 1 and 0 only. */
+int oracle_fcg_mg(int64_t N, const int64_t* rowptr, const int32_t* col, const double* vals, const double* Minv,
+                  int R, const double* f, double* u, double tol, int max_outer, int n_inner, double eps_inner,
+                  int literal_beta, const uint8_t* free_mask, int64_t N4, const int64_t* rowptr4,
+                  const int32_t* col4, const double* vals4, const double* Minv4, const uint8_t* free4,
+                  const int32_t* ends, int n_inner1, double eps_inner1,
+                  int32_t* outer, int32_t* inner_total, int32_t* inner1_total, double* relres) {
+  return oracle_fcg_ml(N, rowptr, col, vals, Minv, R, f, u, tol, max_outer, n_inner, eps_inner, literal_beta,
+                       free_mask, N4, rowptr4, col4, vals4, Minv4, free4, ends, n_inner1, eps_inner1, 0, NULL, NULL,
+                       NULL, NULL, NULL, 0, 0.0, outer, inner_total, inner1_total, NULL, relres);
 }
 
 /* The flexible mixed CG with the inner loop at level 0 only. */

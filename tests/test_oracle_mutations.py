@@ -32,6 +32,8 @@ MUTANTS = {
     "pcg_residual_sign": ("          r[k] -= alpha * q[k];\n        }\n      }\n    apply_blocks(N, R, Minv, r, z);",
                           "          r[k] += alpha * q[k];\n        }\n      }\n    apply_blocks(N, R, Minv, r, z);"),
     "adjoint_sign": ("    g[e] = -acc;", "    g[e] = acc;"),
+    "aggregate_stragglers_to_last": ("    agg[n] = first[best];", "    agg[n] = (int32_t)(count - 1);"),
+    "galerkin_column_aggregate": ("        const int32_t B = agg[b];", "        const int32_t B = agg[a];"),
     "block_jacobi_transposed": ("for (int j = 0; j < 3; ++j) A[i][j] = vals[9 * b + 3 * i + j];",
                                 "for (int j = 0; j < 3; ++j) A[i][j] = vals[9 * b + 3 * j + i] * (i == j ? 1.0 : 0.5);"),
 }
@@ -48,6 +50,8 @@ PINS = [
     pins.test_quadratic_patch_test,
     pins.test_oedometer_exact,
     pins.test_adjoint_gradient_matches_finite_differences,
+    lambda: pins.test_aggregation_is_a_partition_into_connected_aggregates(pins.make_tet4_levels()),
+    lambda: pins.test_galerkin_aggregation_matrix_is_the_triple_product(pins.make_tet4_levels()),
 ]
 
 

@@ -555,3 +555,94 @@ def test_two_level_fcg_matches_direct_and_moves_work_to_the_coarse_level(box8):
     assert rel2[0] <= 1.5e-8 and j2[0] > 0 and j1[0] == 0
     assert np.linalg.norm(u2 - ud) <= 1e-5 * np.linalg.norm(ud)
     assert i2[0] < i1[0] / 2
+
+
+# ---------------------------------------------------------------------------
+# level 2: aggregation coarsening of the TET4 level (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def make_tet4_levels():
+    m = mg.crust_block(shape=(10, 8, 5), h=1000.0, jitter=0.15, seed=2)[0]
+    cm = oracle.coarse_mesh(m)
+    K1 = oracle.assemble4(cm)
+    return m, cm, K1
+
+
+@pytest.fixture(scope="module")
+def tet4_levels():
+    return make_tet4_levels()
+
+
+def test_aggregation_is_a_partition_into_connected_aggregates(tet4_levels):
+    """Every coarse node lies in exactly one aggregate, every aggregate is
+    connected in the matrix graph, and each has a seed whose whole neighbourhood
+    it contains and within two graph steps of which all its members lie (a
+    pass-2 node joins the aggregate of a neighbour), checked by searches written
+    here, independent of the oracle."""
+    m, cm, K1 = tet4_levels
+    agg = oracle.aggregate(K1)
+    N4 = K1.n_nodes
+    assert agg.shape == (N4,) and agg.min() == 0
+    NA = int(agg.max()) + 1
+    assert np.array_equal(np.unique(agg), np.arange(NA))
+    nbr = [K1.col[K1.rowptr[n]:K1.rowptr[n + 1]] for n in range(N4)]
+    for A in range(NA):
+        mem = set(np.nonzero(agg == A)[0].tolist())
+        start = min(mem)
+        seen, todo = {start}, [start]
+        while todo:
+            n = todo.pop()
+            for j in nbr[n].tolist():
+                if j in mem and j not in seen:
+                    seen.add(j)
+                    todo.append(j)
+        assert seen == mem, A
+        seeds = [s for s in mem if set(nbr[s].tolist()) <= mem]
+        assert seeds, A                                              # a seed's whole neighbourhood
+        two_steps = lambda s: set(nbr[s].tolist()).union(*[set(nbr[j].tolist()) for j in nbr[s].tolist()])
+        assert any(mem <= two_steps(s) for s in seeds), A
+    assert N4 / 40 < NA < N4 / 4
+
+
+def test_galerkin_aggregation_matrix_is_the_triple_product(tet4_levels):
+    """A2 equals P2^T K1_bc P2 formed with scipy from an explicit P2 (aggregate
+    value copied to the members' free DOFs), with identity on aggregate DOFs that
+    have no free member; it is symmetric positive definite."""
+    import scipy.sparse as sp
+    m, cm, K1 = tet4_levels
+    agg = oracle.aggregate(K1)
+    A2, free2 = oracle.galerkin_agg(K1, cm.free, agg)
+    N4, NA = K1.n_nodes, A2.n_nodes
+    rows, cols = [], []
+    for n in range(N4):
+        for c in range(3):
+            if cm.free[n, c]:
+                rows.append(3 * n + c)
+                cols.append(3 * agg[n] + c)
+    P = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(3 * N4, 3 * NA))
+    ref = (P.T @ K1.to_scipy() @ P).toarray()
+    fixed2 = np.nonzero(free2.reshape(-1) == 0)[0]
+    ref[fixed2, fixed2] = 1.0
+    got = A2.dense()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    # rows and columns of aggregate DOFs without a free member are exactly unit
+    assert np.array_equal(got[fixed2], np.eye(3 * NA)[fixed2])
+    assert np.array_equal(got[:, fixed2], np.eye(3 * NA)[:, fixed2])
+    assert np.allclose(got, got.T, rtol=0, atol=1e-12 * np.abs(got).max())
+    assert np.linalg.eigvalsh(got).min() > 0
+    for c in range(3):                       # an aggregate DOF is free iff a member DOF is
+        assert np.array_equal(free2[:, c] > 0, np.bincount(agg, weights=cm.free[:, c], minlength=NA) > 0)
+
+
+def test_three_level_fcg_matches_direct_and_reduces_level1_work(tet4_levels):
+    """Levels 2, 1, 0 (Algorithm 1(a)): the direct solution, with fewer level-1
+    steps than levels 1 and 0 alone (level 2 resolves the low-frequency part)."""
+    m, cm, K1 = tet4_levels
+    K = oracle.assemble(m)
+    F = mg.random_vectors(m.n_nodes, 2, seed=12) * 1e9 * m.free[:, None, :]
+    ud = oracle.direct_solve(K, F)
+    u2, o2, i02, i12, i22, rel2 = oracle.fcg_ml(K, F, cm, m.free, K1=K1, levels=2)
+    u3, o3, i03, i13, i23, rel3 = oracle.fcg_ml(K, F, cm, m.free, K1=K1, levels=3)
+    assert np.all(rel3 <= 1.5e-8) and np.all(i23 > 0) and np.all(i22 == 0)
+    assert np.linalg.norm(u3 - ud) <= 1e-5 * np.linalg.norm(ud)
+    assert np.all(i13 < i12)
