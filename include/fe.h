@@ -55,7 +55,9 @@ typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
 typedef enum {
   FE_SOLVER_PCG64 = 0,      /* FP64 CG with 3x3 block Jacobi (the plain baseline) */
   FE_SOLVER_FCG_MIXED = 1,  /* FP64 flexible CG, FP32 inner block-Jacobi CG at level 0 (Algorithm 1) */
-  FE_SOLVER_FCG_MG = 2      /* as FCG_MIXED, with the TET4 inner loop (level 1) before level 0 */
+  FE_SOLVER_FCG_MG = 2,     /* as FCG_MIXED, with the TET4 inner loop (level 1) before level 0 */
+  FE_SOLVER_FCG_AMG = 3     /* Algorithm 1 in full: inner loops at levels 2 (aggregation of the TET4
+                               level), 1 and 0; needs the assembled coarse matrices */
 } fe_solver;
 
 typedef struct fe_mesh fe_mesh;   /* opaque, library-owned */
@@ -77,7 +79,8 @@ typedef struct {
   int32_t coarse_op;     /* FCG_MG level-1 operator: 0 assembled when it fits, else element by
                             element (default); 1 assembled (FE_EINVAL if it does not fit);
                             2 element by element */
-  int32_t pad1;
+  int32_t n_inner2;      /* FCG_AMG: cap on level-2 inner steps per outer iteration (3000) */
+  double eps_inner2;     /* FCG_AMG: level-2 inner stop, the same rule as eps_inner (0.025) */
 } fe_solve_opts;
 
 /* Per-case results of fe_pcg_solve. */
@@ -86,7 +89,9 @@ typedef struct {
   int32_t inner_iters;   /* inner steps summed over outer iterations (0 for PCG64) */
   double relres;         /* true relative residual ||f - K u|| / ||f|| at exit (FP64 product) */
   int32_t status;        /* FE_OK, FE_ENOCONV or FE_EBREAKDOWN for this case */
-  int32_t inner1_iters;  /* level-1 (TET4) inner steps summed over outer iterations (FCG_MG only) */
+  int32_t inner1_iters;  /* level-1 (TET4) inner steps summed over outer iterations (FCG_MG, FCG_AMG) */
+  int32_t inner2_iters;  /* level-2 inner steps summed over outer iterations (FCG_AMG) */
+  int32_t pad;
 } fe_solve_stats;
 
 /* Message of the last failure on this thread ("" if none). */
@@ -97,7 +102,8 @@ const char* fe_version(void);
 
 /* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
  * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1, n_inner1 300,
- * eps_inner1 0.05 (the paper's table of loop settings, levels 0 and 1), coarse_op 0. */
+ * eps_inner1 0.05, n_inner2 3000, eps_inner2 0.025 (the paper's table of loop settings,
+ * levels 0, 1 and 2), coarse_op 0. */
 void fe_solve_opts_default(fe_solve_opts* opts);
 
 /*
@@ -328,6 +334,37 @@ fe_status fe_coarse_prolong(const fe_mesh* mesh, int32_t R, fe_dtype dtype, cons
  *   binv4_dev  device double [N4][3][3], overwritten
  * Fails with FE_EINVAL if a free coarse node has a singular block. */
 fe_status fe_coarse_block_jacobi(const fe_mesh* mesh, double* binv4_dev, void* stream);
+
+/*
+ * Level 2 (Sec. 2 and Algorithm 1(a): inner loop level 2), an algebraic
+ * coarsening of the TET4 level: the coarse nodes are aggregated over the graph
+ * of K1's block pattern in two passes in node order (a node with no aggregated
+ * neighbour starts an aggregate of itself and its neighbours; each remaining
+ * node joins the first-pass aggregate of its lowest-numbered neighbour that has
+ * one). P2 copies an aggregate's value to its members' free DOFs, P2^T sums the
+ * members' free values, and A2 = P2^T K1_bc P2 on aggregate DOFs with a free
+ * member (identity on the others), assembled in FP64 and stored in FP32 3x3
+ * block CSR. Built on first use with the assembled coarse matrix (values again
+ * after fe_mesh_set_log_young). Vectors are [NA][R][3] FP32.
+ */
+
+/* fe_level2_info -- builds level 2 if needed; *n_agg receives NA, agg_host (host
+ * int32 [N4], may be NULL) the aggregate of each coarse node. Synchronous. Fails
+ * with FE_EINVAL if the coarse matrices do not fit in a quarter of free memory. */
+fe_status fe_level2_info(const fe_mesh* mesh, int64_t* n_agg, int32_t* agg_host, void* stream);
+
+/* fe_level2_apply -- y2 = A2 x2, R cases, device float [NA][R][3], not aliased. */
+fe_status fe_level2_apply(const fe_mesh* mesh, int32_t R, const float* x2, float* y2, void* stream);
+
+/* fe_level2_restrict -- r2 = P2^T r4: r4 device float [N4][R][3], r2 [NA][R][3]. */
+fe_status fe_level2_restrict(const fe_mesh* mesh, int32_t R, const float* r4, float* r2, void* stream);
+
+/* fe_level2_prolong -- u4 = P2 u2: u2 device float [NA][R][3], u4 [N4][R][3]. */
+fe_status fe_level2_prolong(const fe_mesh* mesh, int32_t R, const float* u2, float* u4, void* stream);
+
+/* fe_level2_block_jacobi -- the level-2 block Jacobi diag3x3[A2]^-1 (Algorithm 1(a),
+ * set-up), device double [NA][3][3], overwritten. */
+fe_status fe_level2_block_jacobi(const fe_mesh* mesh, double* binv2_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -242,6 +242,7 @@ static void upload_materials(fe_mesh* m, cudaStream_t s) {
   m->coarse.jacobi_ready = false;
   m->coarse.geo_ready = false;
   m->coarse.csr_ready = false;
+  m->coarse.l2_ready = false;
 }
 
 }  // namespace fe
@@ -277,7 +278,8 @@ void fe_solve_opts_default(fe_solve_opts* o) {
   o->n_inner1 = 300;
   o->eps_inner1 = 0.05;
   o->coarse_op = 0;
-  o->pad1 = 0;
+  o->n_inner2 = 3000;
+  o->eps_inner2 = 0.025;
 }
 
 fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,

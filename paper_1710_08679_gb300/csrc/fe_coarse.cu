@@ -461,6 +461,7 @@ void build_coarse(fe_mesh* m, cudaStream_t s) {
     FE_REQUIRE(ends[(size_t)(2 * n)] >= 0, "node %lld belongs to no element (no coarse interpolation)",
                (long long)n);
   for (int64_t v = 0; v < N4; ++v) mk4[(size_t)v] = m->nmask_host[(size_t)vertex[(size_t)v]];
+  c.nmask4_host.assign(mk4.begin(), mk4.end());
   // coarse node -> the edge nodes it ends (counting sort over the fine nodes)
   std::vector<int32_t> adj_ptr((size_t)N4 + 1, 0), adj;
   for (int64_t n = 0; n < N; ++n)
@@ -535,10 +536,10 @@ void build_coarse_geometry(fe_mesh* m, cudaStream_t s) {
   c.geo_ready = true;
 }
 
-bool build_coarse_matrix(fe_mesh* m, cudaStream_t s) {
+bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2) {
   build_coarse(m, s);
   Coarse& c = m->coarse;
-  if (c.csr_ready) return true;
+  if (c.csr_ready && (!level2 || c.l2_ready)) return true;
   const int64_t N4 = c.n_nodes, E = m->n_elem;
   if (!c.csr_pattern) {
     // block pattern: each element couples its 4 corners pairwise
@@ -574,14 +575,17 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s) {
     FE_CUDA(cudaMemcpyAsync(c.rowptr.ptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
     FE_CUDA(cudaMemcpyAsync(c.cols.ptr, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, s));
     FE_CUDA(cudaStreamSynchronize(s));
+    c.rowptr_host = std::move(rowptr);
+    c.cols_host = std::move(cols);
     c.csr_pattern = true;
   }
   // the FP32 matrix stays, the FP64 accumulator is temporary: use the assembled
   // form only where both fit in a quarter of the free memory
   size_t free_b = 0, total_b = 0;
   FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const size_t need = (size_t)c.nnzb * 9 * (sizeof(float) + sizeof(double));
-  if (!c.vals32.ptr && need > free_b / 4) return false;
+  size_t need = (size_t)c.nnzb * 9 * (c.vals32.ptr ? sizeof(double) : sizeof(float) + sizeof(double));
+  if (level2 && !c.l2_ready) need += level2_bytes(m);
+  if (need > free_b / 4) return false;
   DevBuf v64, missing;
   v64.alloc((size_t)c.nnzb * 9 * sizeof(double));
   missing.alloc(sizeof(int));
@@ -599,15 +603,20 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s) {
   FE_CUDA(cudaStreamSynchronize(s));
   FE_REQUIRE(hmiss == 0, "coarse matrix assembly: block outside the pattern");
   c.csr_ready = true;
+  if (level2 && !c.l2_ready) build_level2(m, v64.as<double>(), s);
   return true;
+}
+
+void bcsr_spmv(int64_t n, int R, const int32_t* rowptr, const int32_t* cols, const float* vals, const float* x,
+               float* y, cudaStream_t s, const int* skip) {
+  spmv4_kernel<<<blocks_for(n * R), kThreads, 0, s>>>(n, R, rowptr, cols, vals, x, y, skip);
+  FE_CHECK_LAUNCH();
 }
 
 void coarse_spmv(const fe_mesh* m, int R, const float* x4, float* y4, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
   FE_REQUIRE(c.csr_ready, "coarse matrix not assembled");
-  spmv4_kernel<<<blocks_for(c.n_nodes * R), kThreads, 0, s>>>(c.n_nodes, R, c.rowptr.as<int32_t>(),
-                                                              c.cols.as<int32_t>(), c.vals32.as<float>(), x4, y4, skip);
-  FE_CHECK_LAUNCH();
+  bcsr_spmv(c.n_nodes, R, c.rowptr.as<int32_t>(), c.cols.as<int32_t>(), c.vals32.as<float>(), x4, y4, s, skip);
 }
 
 template <typename T>

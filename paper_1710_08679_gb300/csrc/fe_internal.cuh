@@ -150,6 +150,17 @@ struct Coarse {
   int64_t nnzb = 0;
   DevBuf rowptr, cols;      // int32 [N4 + 1], [nnzb] (columns sorted per row)
   DevBuf vals32;            // float [nnzb][9]
+  std::vector<int32_t> rowptr_host, cols_host, nmask4_host;  // host copies for the level-2 set-up
+  // level 2: aggregation of the coarse nodes and its Galerkin matrix A2
+  bool l2_pattern = false, l2_ready = false;
+  int64_t n_agg = 0, nnzb2 = 0;
+  DevBuf agg;               // int32 [N4] aggregate of each coarse node
+  DevBuf mptr, members;     // int32 [NA + 1], [N4]: member nodes of each aggregate
+  DevBuf nmask2;            // uint8 [NA] free-DOF bits of the aggregates
+  DevBuf pos2;              // int32 [nnzb] position in A2 of each K1 block
+  DevBuf rowptr2, cols2;    // int32 [NA + 1], [nnzb2] (columns sorted per row)
+  DevBuf vals2_32;          // float [nnzb2][9]
+  DevBuf binv2_64, binv2_32;  // [NA][9] inverse diagonal blocks of A2
 };
 
 struct SolverWork;  // defined in fe_solver.cu
@@ -228,8 +239,18 @@ void free_solver_work(fe_mesh* m);
 void build_coarse(fe_mesh* m, cudaStream_t s);
 void build_coarse_jacobi(fe_mesh* m, cudaStream_t s);
 void build_coarse_geometry(fe_mesh* m, cudaStream_t s);
-bool build_coarse_matrix(fe_mesh* m, cudaStream_t s);  // false: not enough device memory
+// false: not enough device memory. With level2, also builds the aggregation level.
+bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2 = false);
 void coarse_spmv(const fe_mesh* m, int R, const float* x4, float* y4, cudaStream_t s, const int* skip = nullptr);
+// y = A x for a 3x3 block CSR matrix, R cases of [n][R][3] FP32 vectors
+void bcsr_spmv(int64_t n, int R, const int32_t* rowptr, const int32_t* cols, const float* vals, const float* x,
+               float* y, cudaStream_t s, const int* skip);
+
+// Level 2 (fe_level2.cu)
+void build_level2(fe_mesh* m, const double* k1_64, cudaStream_t s);  // K1 blocks in FP64, unmasked
+size_t level2_bytes(const fe_mesh* m);                                 // device bytes level 2 will need
+void level2_restrict(const fe_mesh* m, int R, const float* r4, float* r2, cudaStream_t s, const int* skip = nullptr);
+void level2_prolong(const fe_mesh* m, int R, const float* u2, float* u4, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 void ebe4_apply(const fe_mesh* m, int R, const T* x4, T* y4, cudaStream_t s, const int* skip = nullptr);
 template <typename T>

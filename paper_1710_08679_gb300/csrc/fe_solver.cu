@@ -12,12 +12,18 @@
 //    solved there by the same FP32 CG with the TET4 operator and its own block
 //    Jacobi, and the coarse solution is prolonged as the initial guess of the
 //    level-0 loop (Algorithm 1(a), inner loop level 1).
+//  * FE_SOLVER_FCG_AMG: as FCG_MG with the aggregation level first: the level-1
+//    residual and guess are restricted to the aggregates, solved there by the
+//    same FP32 CG with A2 and its block Jacobi, and prolonged as the initial
+//    guess of the level-1 loop (Algorithm 1(a), inner loop level 2).
 //
 // GPU design: every per-case scalar (rho, gamma, alpha, beta, norms, masks)
 // lives in device arrays of length R; kernels read them directly, so one outer
 // iteration (including all N inner steps) runs without host round trips and is
-// captured once as a CUDA graph and replayed. Inner steps after the inner stop
-// test fires become no-ops (each kernel checks a device flag). Each case is
+// captured once as a CUDA graph and replayed. Each inner loop is a while node
+// of that graph whose condition the stop-test kernel sets, so it runs only the
+// steps it needs; without a graph, the steps after the stop return at once
+// (each kernel checks a device flag). Each case is
 // masked on its own once it converges. Vectors are [N][R][3]; a vector kernel's
 // thread handles one (node, case) pair and neighbouring threads touch
 // neighbouring addresses. Dot products accumulate per thread (FP32 products in
@@ -40,9 +46,9 @@ namespace fe {
 // ---------------------------------------------------------------------------
 enum DField {
   D_FN2 = 0, D_RN2, D_RHO, D_GAM, D_ZQ, D_PQP, D_RHOP, D_ALPHA, D_BETA,
-  D_RBN2, D_EN2, D_RHOA, D_RHOB, D_GAMI, D_ALPHAI, D_BETAI, D_RT2, D_RELRES, D_RBN21, D_COUNT
+  D_RBN2, D_EN2, D_RHOA, D_RHOB, D_GAMI, D_ALPHAI, D_BETAI, D_RT2, D_RELRES, D_RBN21, D_RBN22, D_COUNT
 };
-enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INNER, I_INNER1, I_COUNT };
+enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INNER, I_INNER1, I_INNER2, I_COUNT };
 
 struct Cases {
   double* d;      // [D_COUNT][R]
@@ -60,6 +66,7 @@ struct SolverWork {
   DevBuf r, p, q;                 // double [N][R][3]
   DevBuf rb, ub, eb, pb, qb;      // float  [N][R][3]
   DevBuf rb1, ub1, eb1, pb1, qb1; // float  [N4][R][3] (level 1, allocated when used)
+  DevBuf rb2, ub2, eb2, pb2, qb2; // float  [NA][R][3] (level 2, allocated when used)
   DevBuf tu, tq;                  // double [N][3] (single-case true residual)
   DevBuf d, i;                    // case state
   cudaStream_t stream = nullptr;
@@ -590,6 +597,7 @@ __global__ void s_slot_start(Cases C, int r, int pcg) {
   C.I(I_OUTER, r) = 0;
   C.I(I_INNER, r) = 0;
   C.I(I_INNER1, r) = 0;
+  C.I(I_INNER2, r) = 0;
   C.D(D_RELRES, r) = 0.0;
 }
 
@@ -678,6 +686,7 @@ __global__ void s_outer_begin(Cases C) {
   const int r = threadIdx.x;
   C.D(D_RBN2, r) = 0.0;
   C.D(D_RBN21, r) = 0.0;
+  C.D(D_RBN22, r) = 0.0;
   C.D(D_EN2, r) = 0.0;
   C.D(D_RHOA, r) = 0.0;
   C.D(D_ZQ, r) = 0.0;
@@ -813,6 +822,8 @@ struct Solve {
   size_t sm;  // shared bytes of reducing vector kernels
   int64_t N1 = 0;  // level-1 nodes (0: no coarse level)
   VGeom g1;
+  int64_t N2 = 0;  // level-2 aggregates (0: no level 2)
+  VGeom g2;
   bool assembled1 = false;  // level-1 operator: assembled block CSR, else element by element
   cudaStream_t s;
   const double* f;
@@ -891,16 +902,19 @@ struct Level {
   const VGeom* g;
   const float* B;                 // FP32 inverse diagonal blocks [N][9]
   float *rb, *ub, *eb, *pb, *qb;  // [N][R][3]
-  bool coarse;                    // operator: TET4 (level 1) or TET10 (level 0)
+  int level;                      // operator: TET10 (0), TET4 (1) or aggregation (2)
   int n;
   double eps;
   int f_rbn2, f_count;
 };
 
 static void level_apply(Solve& S, const Level& L, const float* x, float* y, const int* skip) {
-  if (L.coarse && S.assembled1)
+  const Coarse& c = S.m->coarse;
+  if (L.level == 2)
+    bcsr_spmv(c.n_agg, S.R, c.rowptr2.as<int32_t>(), c.cols2.as<int32_t>(), c.vals2_32.as<float>(), x, y, S.s, skip);
+  else if (L.level == 1 && S.assembled1)
     coarse_spmv(S.m, S.R, x, y, S.s, skip);
-  else if (L.coarse)
+  else if (L.level == 1)
     ebe4_apply<float>(S.m, S.R, x, y, S.s, skip);
   else
     ebe_apply<float>(S.m, S.R, x, y, S.s, skip);
@@ -972,18 +986,30 @@ static void fcg_iteration(Solve& S) {
   S.vec(k_cast_start, B32, w->r.as<double>(), w->rb.as<float>(), w->ub.as<float>());
   if (S.N1 > 0) {
     Level L1{S.N1, &S.g1, m->coarse.binv32.as<float>(), w->rb1.as<float>(), w->ub1.as<float>(),
-             w->eb1.as<float>(), w->pb1.as<float>(), w->qb1.as<float>(), true, S.o.n_inner1, S.o.eps_inner1,
+             w->eb1.as<float>(), w->pb1.as<float>(), w->qb1.as<float>(), 1, S.o.n_inner1, S.o.eps_inner1,
              (int)D_RBN21, (int)I_INNER1};
     coarse_restrict<float>(m, S.R, w->rb.as<float>(), L1.rb, S.s);
     coarse_restrict<float>(m, S.R, w->ub.as<float>(), L1.ub, S.s);
     S.vec_on(L1.N, *L1.g, k_dot<float>, (int)D_RBN21, (const int*)nullptr, (const float*)L1.rb,
              (const float*)L1.rb);
+    if (S.N2 > 0) {
+      Level L2{S.N2, &S.g2, m->coarse.binv2_32.as<float>(), w->rb2.as<float>(), w->ub2.as<float>(),
+               w->eb2.as<float>(), w->pb2.as<float>(), w->qb2.as<float>(), 2, S.o.n_inner2, S.o.eps_inner2,
+               (int)D_RBN22, (int)I_INNER2};
+      level2_restrict(m, S.R, L1.rb, L2.rb, S.s);
+      level2_restrict(m, S.R, L1.ub, L2.ub, S.s);
+      S.vec_on(L2.N, *L2.g, k_dot<float>, (int)D_RBN22, (const int*)nullptr, (const float*)L2.rb,
+               (const float*)L2.rb);
+      inner_loop(S, L2);
+      level2_prolong(m, S.R, (const float*)L2.ub, L1.ub, S.s);
+      S.scal(s_level_begin);
+    }
     inner_loop(S, L1);
     coarse_prolong<float>(m, S.R, (const float*)L1.ub, w->ub.as<float>(), S.s);
     S.scal(s_level_begin);
   }
   Level L0{S.N, &S.g, B32, w->rb.as<float>(), w->ub.as<float>(), w->eb.as<float>(), w->pb.as<float>(),
-           w->qb.as<float>(), false, S.o.n_inner, S.o.eps_inner, (int)D_RBN2, (int)I_INNER};
+           w->qb.as<float>(), 0, S.o.n_inner, S.o.eps_inner, (int)D_RBN2, (int)I_INNER};
   inner_loop(S, L0);
   S.vec(k_outer_zq, (const float*)w->ub.as<float>(), (const double*)w->q.as<double>());
   S.scal(s_outer_beta, S.o.literal_beta);
@@ -1045,11 +1071,24 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   S.u = u;
   S.o = o;
   const bool pcg = o.solver == FE_SOLVER_PCG64;
-  if (o.solver == FE_SOLVER_FCG_MG) {
+  if (o.solver == FE_SOLVER_FCG_MG || o.solver == FE_SOLVER_FCG_AMG) {
+    const bool amg = o.solver == FE_SOLVER_FCG_AMG;
     build_coarse_jacobi(m, s);
-    S.assembled1 = o.coarse_op != 2 && build_coarse_matrix(m, s);
+    S.assembled1 = (amg || o.coarse_op != 2) && build_coarse_matrix(m, s, amg);
+    FE_REQUIRE(!amg || S.assembled1, "level 2 needs the assembled coarse matrices: not enough free device memory");
     FE_REQUIRE(o.coarse_op != 1 || S.assembled1, "not enough free device memory for the assembled coarse matrix");
     if (!S.assembled1) build_coarse_geometry(m, s);
+    if (amg) {
+      S.N2 = m->coarse.n_agg;
+      S.g2 = vgeom(S.N2, R, sms);
+      const size_t v2 = (size_t)S.N2 * R * 3 * sizeof(float);
+      for (DevBuf* b : {&w->rb2, &w->ub2, &w->eb2, &w->pb2, &w->qb2})
+        if (b->bytes != v2) {
+          b->release();
+          b->alloc(v2);
+        }
+      FE_CUDA(cudaMemsetAsync(w->pb2.ptr, 0, v2, s));
+    }
     S.N1 = m->coarse.n_nodes;
     S.g1 = vgeom(S.N1, R, sms);
     const size_t v1 = (size_t)S.N1 * R * 3 * sizeof(float);
@@ -1150,6 +1189,8 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
             many->stats[cs].relres = rel;
             many->stats[cs].status = st;
             many->stats[cs].inner1_iters = hi[I_INNER1 * R + r];
+            many->stats[cs].inner2_iters = hi[I_INNER2 * R + r];
+            many->stats[cs].pad = 0;
           }
           if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
           else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
@@ -1202,6 +1243,8 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
         stats[c].relres = rel;
         stats[c].status = st;
         stats[c].inner1_iters = hi[I_INNER1 * R + c];
+        stats[c].inner2_iters = hi[I_INNER2 * R + c];
+        stats[c].pad = 0;
       }
       if (st == FE_EBREAKDOWN) result = FE_EBREAKDOWN;
       else if (st == FE_ENOCONV && result == FE_OK) result = FE_ENOCONV;
@@ -1220,13 +1263,16 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
 }
 
 static void check_opts(const fe_solve_opts& o) {
-  FE_REQUIRE(o.solver == FE_SOLVER_PCG64 || o.solver == FE_SOLVER_FCG_MIXED || o.solver == FE_SOLVER_FCG_MG,
-             "unknown solver %d", o.solver);
+  FE_REQUIRE(o.solver >= FE_SOLVER_PCG64 && o.solver <= FE_SOLVER_FCG_AMG, "unknown solver %d", o.solver);
   FE_REQUIRE(o.tol > 0.0 && o.tol < 1.0, "tol must lie in (0, 1)");
   FE_REQUIRE(o.max_outer >= 1, "max_outer must be >= 1");
   FE_REQUIRE(o.n_inner >= 0 && o.n_inner <= 100000, "n_inner out of range");
   FE_REQUIRE(o.eps_inner >= 0.0, "eps_inner must be >= 0");
-  if (o.solver == FE_SOLVER_FCG_MG) {
+  if (o.solver == FE_SOLVER_FCG_AMG) {
+    FE_REQUIRE(o.n_inner2 >= 0 && o.n_inner2 <= 100000, "n_inner2 out of range");
+    FE_REQUIRE(o.eps_inner2 >= 0.0, "eps_inner2 must be >= 0");
+  }
+  if (o.solver == FE_SOLVER_FCG_MG || o.solver == FE_SOLVER_FCG_AMG) {
     FE_REQUIRE(o.n_inner1 >= 0 && o.n_inner1 <= 100000, "n_inner1 out of range");
     FE_REQUIRE(o.eps_inner1 >= 0.0, "eps_inner1 must be >= 0");
     FE_REQUIRE(o.coarse_op >= 0 && o.coarse_op <= 2, "coarse_op must be 0, 1 or 2");

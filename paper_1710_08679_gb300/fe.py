@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libfe.so")
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT = range(7)
 FE_F64, FE_F32 = 0, 1
-FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED, FE_SOLVER_FCG_MG = 0, 1, 2
-SOLVERS = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED, "fcg_mg": FE_SOLVER_FCG_MG}
+FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED, FE_SOLVER_FCG_MG, FE_SOLVER_FCG_AMG = 0, 1, 2, 3
+SOLVERS = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED, "fcg_mg": FE_SOLVER_FCG_MG,
+           "fcg_amg": FE_SOLVER_FCG_AMG}
 COARSE_OPS = {"auto": 0, "assembled": 1, "ebe": 2}
 EBE_DIRECT, EBE_TILED = 0, 1
 
@@ -31,7 +32,8 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
             "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
-            "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply"]
+            "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
+            "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi"]
 
 
 class FeError(RuntimeError):
@@ -45,12 +47,13 @@ class SolveOpts(ctypes.Structure):
                 ("n_inner", ctypes.c_int32), ("eps_inner", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("n_inner1", ctypes.c_int32), ("eps_inner1", ctypes.c_double), ("coarse_op", ctypes.c_int32),
-                ("pad1", ctypes.c_int32)]
+                ("n_inner2", ctypes.c_int32), ("eps_inner2", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("status", ctypes.c_int32), ("inner1_iters", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("inner1_iters", ctypes.c_int32), ("inner2_iters", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,10 +96,16 @@ def load(path: Optional[str] = None):
     lib.fe_coarse_prolong.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     lib.fe_coarse_block_jacobi.argtypes = [_vp, _vp, _vp]
     lib.fe_coarse_apply.argtypes = [_vp, _i32, _vp, _vp, _vp]
+    lib.fe_level2_info.argtypes = [_vp, ctypes.POINTER(_i64), _vp, _vp]
+    for name in ("fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong"):
+        getattr(lib, name).argtypes = [_vp, _i32, _vp, _vp, _vp]
+    lib.fe_level2_block_jacobi.argtypes = [_vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
-                 "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply"):
+                 "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
+                 "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
+                 "fe_level2_block_jacobi"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -231,7 +240,7 @@ class Mesh:
     def solve(self, f, u0=None, solver: str = "fcg_mixed", tol: float = 1e-8, max_outer: int = 20000,
               n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
               check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
-              raise_on_fail: bool = True):
+              n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True):
         """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status)."""
         torch = _torch()
         R = int(f.shape[1])
@@ -245,10 +254,11 @@ class Mesh:
         o.use_graph, o.literal_beta, o.check_every = int(bool(use_graph)), int(bool(literal_beta)), int(check_every)
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         o.coarse_op = COARSE_OPS[coarse_op]
+        o.n_inner2, o.eps_inner2 = int(n_inner2), float(eps_inner2)
         stats = (SolveStats * R)()
         st = load().fe_pcg_solve(self._h, R, fp, up, ctypes.byref(o), stats, self._stream())
-        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, relres=s.relres,
-                    status=s.status) for s in stats]
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, inner2=s.inner2_iters,
+                    relres=s.relres, status=s.status) for s in stats]
         if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
             _check(st, "fe_pcg_solve")
         return u, out, st
@@ -256,7 +266,7 @@ class Mesh:
     def solve_many(self, f_cases, R_slots: int = 0, solver: str = "fcg_mixed", tol: float = 1e-8,
                    max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
                    n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
-                   raise_on_fail: bool = True):
+                   n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True):
         """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
         in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
         torch = _torch()
@@ -270,12 +280,13 @@ class Mesh:
         o.use_graph = int(bool(use_graph))
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         o.coarse_op = COARSE_OPS[coarse_op]
+        o.n_inner2, o.eps_inner2 = int(n_inner2), float(eps_inner2)
         stats = (SolveStats * n)()
         r_used = _i32()
         st = load().fe_solve_many(self._h, n, fp, ctypes.c_void_p(u.data_ptr()), int(R_slots), ctypes.byref(o),
                                   stats, ctypes.byref(r_used), self._stream())
-        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, relres=s.relres,
-                    status=s.status) for s in stats]
+        out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, inner2=s.inner2_iters,
+                    relres=s.relres, status=s.status) for s in stats]
         if st not in (FE_OK, FE_ENOCONV, FE_EBREAKDOWN) or (raise_on_fail and st != FE_OK):
             _check(st, "fe_solve_many")
         return u, out, st, r_used.value
@@ -347,6 +358,50 @@ class Mesh:
         out = torch.empty((self._n4(), 3, 3), dtype=torch.float64, device=f"cuda:{self.device}")
         _check(load().fe_coarse_block_jacobi(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()),
                "fe_coarse_block_jacobi")
+        return out
+
+    # ---- level 2 (aggregation of the TET4 level) --------------------------
+    def level2_info(self):
+        """(NA, agg): aggregate count and the aggregate of each coarse node."""
+        na = _i64()
+        _check(load().fe_level2_info(self._h, ctypes.byref(na), None, self._stream()), "fe_level2_info")
+        agg = np.empty(self._n4(), dtype=np.int32)
+        _check(load().fe_level2_info(self._h, ctypes.byref(na), agg.ctypes.data, self._stream()), "fe_level2_info")
+        self.n_agg = int(na.value)
+        return self.n_agg, agg
+
+    def _na(self) -> int:
+        if getattr(self, "n_agg", None) is None:
+            self.level2_info()
+        return self.n_agg
+
+    def _level2_vec(self, fn: str, x, n_in: int, n_out: int):
+        torch = _torch()
+        if x.dim() != 3 or x.shape[0] != n_in or x.shape[2] != 3:
+            raise ValueError(f"input must be [{n_in}, R, 3]")
+        xp = _dev_ptr(x, torch.float32, name="input")
+        y = torch.empty((n_out, int(x.shape[1]), 3), dtype=torch.float32, device=x.device)
+        _check(getattr(load(), fn)(self._h, int(x.shape[1]), xp, ctypes.c_void_p(y.data_ptr()), self._stream()), fn)
+        return y
+
+    def level2_apply(self, x2):
+        """y2 = A2 x2 (FP32), x2 [NA, R, 3]."""
+        return self._level2_vec("fe_level2_apply", x2, self._na(), self._na())
+
+    def level2_restrict(self, r4):
+        """r2 = P2^T r4: [N4, R, 3] -> [NA, R, 3] (FP32)."""
+        return self._level2_vec("fe_level2_restrict", r4, self._n4(), self._na())
+
+    def level2_prolong(self, u2):
+        """u4 = P2 u2: [NA, R, 3] -> [N4, R, 3] (FP32)."""
+        return self._level2_vec("fe_level2_prolong", u2, self._na(), self._n4())
+
+    def level2_block_jacobi(self):
+        """Inverse 3x3 diagonal blocks of A2, float64 [NA, 3, 3]."""
+        torch = _torch()
+        out = torch.empty((self._na(), 3, 3), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(load().fe_level2_block_jacobi(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()),
+               "fe_level2_block_jacobi")
         return out
 
     def adjoint_grad(self, u, lam):
