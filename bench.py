@@ -48,13 +48,14 @@ def parse():
                     help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
-    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer"],
+    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer", "coarse"],
                     help="ebe: the EBE line on the 70x70x35 crust block (default); many: 96 unit-slip cases on "
                          "the 120x120x60 block through fe_solve_many vs the plain FP64 PCG one case at a time")
     ap.add_argument("--many-cases", type=int, default=96, help="cases of --workload many")
     ap.add_argument("--many-plain", type=int, default=1, help="cases timed with the plain FP64 PCG")
-    ap.add_argument("--many-solver", choices=["fcg_mixed", "fcg_mg"], default="fcg_mixed",
-                    help="many-case solver: inner loop at level 0 only, or with the TET4 level 1 first")
+    ap.add_argument("--many-solver", choices=["fcg_mixed", "fcg_mg", "fcg_amg"], default="fcg_mixed",
+                    help="many-case solver: inner loop at level 0 only, with the TET4 level 1 first, or with "
+                         "levels 2 and 1 first")
     return ap.parse_args()
 
 
@@ -509,8 +510,9 @@ def run_many(args):
     # before the timed region; fe_solve_many would otherwise tune on first use
     for RR, dt in ((32, "f32"), (32, "f64"), (1, "f64")):
         M.tune(RR, dt)
-    if args.many_solver == "fcg_mg":
+    if args.many_solver in ("fcg_mg", "fcg_amg"):
         M.coarse_block_jacobi()
+        M.coarse_matrix_info()          # assembled coarse matrices (and level 2) before the timed call
     setup_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -536,6 +538,7 @@ def run_many(args):
            "many": {"seconds": t_many, "status": int(st), "all_converged": all(s["relres"] <= 1e-8 for s in stats),
                     "outer_min_max": [min(s["outer"] for s in stats), max(s["outer"] for s in stats)],
                     "inner0_total": sum(s["inner"] for s in stats), "inner1_total": sum(s["inner1"] for s in stats),
+                    "inner2_total": sum(s["inner2"] for s in stats),
                     "relres_max": max(s["relres"] for s in stats)},
            "plain_pcg64_one_case": {"case_solves_per_s": plain_rate, "cases": plain},
            "speedup": rate / plain_rate if plain_rate else None}
@@ -569,6 +572,58 @@ def run_two_layer(args):
     print(json.dumps(out), flush=True)
 
 
+def run_coarse(args):
+    """The level-1 (TET4) and level-2 (aggregation) operators at R = 16, FP32, on
+    the 70x70x35 crust block: assembled K1_bc product, TET4 element-by-element
+    product, transfers, and the A2 product; CUDA events over --steps launches of
+    each after --warmup. The assembled product's roofline: algorithmic bytes =
+    blocks (36 B + 4 B column) + row pointers + x read once + y written once."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08679_gb300 import fe
+    from paper_1710_08679_gb300 import meshgen as mg
+    shape = SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x"))
+    m, _ = mg.crust_block(shape=shape)
+    M = fe.Mesh.from_mesh(m)
+    R = R_MAIN
+    n4 = M.coarse_info()[0]
+    na = M.level2_info()[0]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x4 = torch.randn((n4, R, 3), generator=g, device="cuda", dtype=torch.float32)
+    x10 = torch.randn((m.n_nodes, R, 3), generator=g, device="cuda", dtype=torch.float32)
+    x2 = torch.randn((na, R, 3), generator=g, device="cuda", dtype=torch.float32)
+    ops = {"assembled_K1": lambda: M.coarse_apply(x4), "tet4_ebe": lambda: M.ebe4(x4),
+           "restrict_P1T": lambda: M.coarse_restrict(x10), "prolong_P1": lambda: M.coarse_prolong(x4),
+           "A2": lambda: M.level2_apply(x2), "restrict_P2T": lambda: M.level2_restrict(x4),
+           "prolong_P2": lambda: M.level2_prolong(x2)}
+    res = {}
+    for name, fn in ops.items():
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    nnzb, nnzb2 = M.coarse_matrix_info()
+    bytes_k1 = nnzb * 40 + (n4 + 1) * 4 + 2 * n4 * R * 12
+    gbs = bytes_k1 / (res["assembled_K1_ms"] * 1e-3) / 1e9
+    hbm, hbm_src = load_peaks()
+    out = {"metric": "coarse-level operator time (ms per product)", "unit": "ms", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "crust_%dx%dx%d_tet10 coarse levels" % shape, "R": R, "coarse_nodes": n4,
+                      "coarse_blocks": nnzb, "aggregates": na, "level2_blocks": nnzb2, "steps": args.steps,
+                      "warmup": args.warmup},
+           "times": res,
+           "roofline_assembled_K1": {"bound": "hbm", "achieved": gbs, "peak": hbm, "peak_source": hbm_src,
+                                     "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": bytes_k1}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -577,6 +632,8 @@ def main():
         run_many(args)
     elif args.workload == "two_layer":
         run_two_layer(args)
+    elif args.workload == "coarse":
+        run_coarse(args)
     else:
         run_ours(args)
 

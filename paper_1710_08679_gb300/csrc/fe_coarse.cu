@@ -359,6 +359,45 @@ __global__ void __launch_bounds__(kThreads) spmv4_kernel(int64_t N4, int R, cons
   ya[2] = y2;
 }
 
+// the same product with 4 cases per thread (R a multiple of 4): each block is
+// loaded once for 4 cases and the 12 x values of a column node come as three
+// 16-byte loads (48-byte aligned: (b R + r0) is a multiple of 4)
+__global__ void __launch_bounds__(kThreads) spmv4_group_kernel(int64_t N4, int R, const int32_t* __restrict__ rowptr,
+                                                               const int32_t* __restrict__ cols,
+                                                               const float* __restrict__ vals,
+                                                               const float* __restrict__ x, float* __restrict__ y,
+                                                               const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int G = R / 4;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= N4 * G) return;
+  const int64_t a = gid / G;
+  const int r0 = (int)(gid - a * G) * 4;
+  float acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = 0.f;
+  const int q1 = __ldg(rowptr + a + 1);
+  for (int q = __ldg(rowptr + a); q < q1; ++q) {
+    const int64_t b = __ldg(cols + q);
+    const float* B = vals + 9 * (int64_t)q;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = __ldg(B + k);
+    const float4* xb = reinterpret_cast<const float4*>(x + (b * R + r0) * 3);
+    const float4 v0 = __ldg(xb), v1 = __ldg(xb + 1), v2 = __ldg(xb + 2);
+    const float v[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        acc[3 * w + i] += m[3 * i] * v[3 * w] + m[3 * i + 1] * v[3 * w + 1] + m[3 * i + 2] * v[3 * w + 2];
+  }
+  float4* o = reinterpret_cast<float4*>(y + (a * R + r0) * 3);
+  o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  o[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+}
+
 // diagonal 3x3 blocks of K1: V [(lam + mu) g_a g_a^T + mu |g_a|^2 I] per corner
 __global__ void jacobi4_diag_kernel(MeshView<double> M, const int32_t* __restrict__ conn4, double* __restrict__ Dg) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -609,7 +648,11 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2) {
 
 void bcsr_spmv(int64_t n, int R, const int32_t* rowptr, const int32_t* cols, const float* vals, const float* x,
                float* y, cudaStream_t s, const int* skip) {
-  spmv4_kernel<<<blocks_for(n * R), kThreads, 0, s>>>(n, R, rowptr, cols, vals, x, y, skip);
+  if (R % 4 == 0) {
+    spmv4_group_kernel<<<blocks_for(n * (R / 4)), kThreads, 0, s>>>(n, R, rowptr, cols, vals, x, y, skip);
+  } else {
+    spmv4_kernel<<<blocks_for(n * R), kThreads, 0, s>>>(n, R, rowptr, cols, vals, x, y, skip);
+  }
   FE_CHECK_LAUNCH();
 }
 

@@ -297,6 +297,17 @@ extern "C" fe_status fe_level2_info(const fe_mesh* mesh, int64_t* n_agg, int32_t
   });
 }
 
+extern "C" fe_status fe_coarse_matrix_info(const fe_mesh* mesh, int64_t* n_blocks1, int64_t* n_blocks2,
+                                           void* stream) {
+  return fe::guarded([&] {
+    FE_REQUIRE(mesh != nullptr, "mesh is NULL");
+    fe::DeviceGuard dg(mesh->device);
+    fe_mesh* m = level2_ready(mesh, (cudaStream_t)stream);
+    if (n_blocks1) *n_blocks1 = m->coarse.nnzb;
+    if (n_blocks2) *n_blocks2 = m->coarse.nnzb2;
+  });
+}
+
 extern "C" fe_status fe_level2_apply(const fe_mesh* mesh, int32_t R, const float* x2, float* y2, void* stream) {
   return fe::guarded([&] {
     vec_args(R, x2, y2);

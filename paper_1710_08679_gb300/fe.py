@@ -33,7 +33,7 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
             "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
-            "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi"]
+            "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info"]
 
 
 class FeError(RuntimeError):
@@ -100,12 +100,13 @@ def load(path: Optional[str] = None):
     for name in ("fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong"):
         getattr(lib, name).argtypes = [_vp, _i32, _vp, _vp, _vp]
     lib.fe_level2_block_jacobi.argtypes = [_vp, _vp, _vp]
+    lib.fe_coarse_matrix_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
                  "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
                  "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
-                 "fe_level2_block_jacobi"):
+                 "fe_level2_block_jacobi", "fe_coarse_matrix_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -383,6 +384,13 @@ class Mesh:
         y = torch.empty((n_out, int(x.shape[1]), 3), dtype=torch.float32, device=x.device)
         _check(getattr(load(), fn)(self._h, int(x.shape[1]), xp, ctypes.c_void_p(y.data_ptr()), self._stream()), fn)
         return y
+
+    def coarse_matrix_info(self):
+        """(blocks of K1_bc, blocks of A2), building the assembled coarse matrices if needed."""
+        a, b = _i64(), _i64()
+        _check(load().fe_coarse_matrix_info(self._h, ctypes.byref(a), ctypes.byref(b), self._stream()),
+               "fe_coarse_matrix_info")
+        return int(a.value), int(b.value)
 
     def level2_apply(self, x2):
         """y2 = A2 x2 (FP32), x2 [NA, R, 3]."""
