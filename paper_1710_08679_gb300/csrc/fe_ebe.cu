@@ -1102,10 +1102,12 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
     auto it = m->tilings.find(tile);
     FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
     if (kind == FE_EBE_GATHER_DF) {
-      FE_REQUIRE(sizeof(T) == 8, "the float-float kernel computes FP64 products only");
-      FE_REQUIRE(launch_pipe_df(m, *it->second, R, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
-                                s, skip),
-                 "float-float kernel unavailable for R = %d with tiles of %d elements", R, tile);
+      if constexpr (sizeof(T) == 8) {
+        FE_REQUIRE(launch_pipe_df(m, *it->second, R, x, y, s, skip),
+                   "float-float kernel unavailable for R = %d with tiles of %d elements", R, tile);
+      } else {
+        FE_REQUIRE(false, "the float-float kernel computes FP64 products only");
+      }
     } else if (kind == FE_EBE_GATHER) {
       if (launch_pipe<T>(m, *it->second, R, x, y, s, skip)) return;
       zero_pass<T>(m, R, y, s, skip);
