@@ -58,6 +58,15 @@ __device__ __forceinline__ df& operator+=(df& a, const df& b) {
   return a;
 }
 
+// The rare cases of the two conversions below (values outside the float range,
+// sums crossing a binade) take the FP64 conversion or addition. They live in
+// functions that are never inlined: inlined, the compiler evaluates such a
+// one-instruction branch for every value and selects the result, which puts an
+// FP64-rate instruction on every conversion.
+__device__ __noinline__ df df_split_rare(double x) { return df(__double2float_rn(x), 0.f); }
+
+__device__ __noinline__ double df_add_rare(float hi, float lo) { return (double)hi + (double)lo; }
+
 // Double -> float-float with integer operations only. (On GB300 the double to
 // float conversion and double additions run at the FP64 rate, 1/61 of FP32.)
 // hi: the double rounded to 24 significant bits (round half away from zero, by
@@ -69,10 +78,10 @@ __device__ __forceinline__ df df_split(double x) {
   const long long b = __double_as_longlong(x);
   const long long mag = b & 0x7FFFFFFFFFFFFFFFLL;
   const int e = (int)(mag >> 52);                                  // biased double exponent
-  if (e < 1023 - 126 || e > 1023 + 127) return df(__double2float_rn(x), 0.f);  // rare: out of float range
+  if (e < 1023 - 126 || e > 1023 + 127) return df_split_rare(x);   // rare: out of float range
   const long long rmag = (mag + (1LL << 28)) & ~((1LL << 29) - 1);  // magnitude rounded to 24 bits
   const int re = (int)(rmag >> 52);
-  if (re > 1023 + 127) return df(__double2float_rn(x), 0.f);
+  if (re > 1023 + 127) return df_split_rare(x);
   const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
   const float hi = __int_as_float((int)(sign | (unsigned)((re - 1023 + 127) << 23) |
                                         (unsigned)((rmag >> 29) & 0x7FFFFF)));
@@ -86,20 +95,23 @@ __device__ __forceinline__ df df_split(double x) {
   return df(hi, lo);
 }
 
-// Float-float -> double: (double)hi (a fast conversion) plus lo counted in units
-// of that double's last place, added to its bit pattern. If the sum crosses into
-// another binade the exact double addition is used instead (rare).
+// Float-float -> double: hi widened to double by rebuilding its bit pattern
+// (exact for normal floats), plus lo counted in units of that double's last
+// place and added to the pattern. Zero, subnormal, infinite and NaN hi, and sums
+// that cross into another binade, take the exact double addition (rare).
 __device__ __forceinline__ double df_to_double(const df& a) {
-  const double d = (double)a.hi;
-  if (a.lo == 0.f) return d;
-  const int eh = (int)((__float_as_uint(a.hi) >> 23) & 0xFF);       // biased float exponent of hi
-  // the ulp of d is 2^(eh - 127 - 52); its inverse 2^(179 - eh) is a normal float for eh >= 52
-  if (eh < 52 || eh == 255) return d + (double)a.lo;
+  const unsigned hb = __float_as_uint(a.hi);
+  const int eh = (int)((hb >> 23) & 0xFF);                          // biased float exponent of hi
+  // the ulp of the double is 2^(eh - 127 - 52); its inverse 2^(179 - eh) is a normal float for eh >= 52
+  if (eh < 52 || eh == 255) return df_add_rare(a.hi, a.lo);
+  const long long db = (long long)((unsigned long long)(hb >> 31) << 63 |
+                                   (unsigned long long)(eh - 127 + 1023) << 52 |
+                                   (unsigned long long)(hb & 0x7FFFFFu) << 29);
+  if (a.lo == 0.f) return __longlong_as_double(db);
   const float scale = __int_as_float((306 - eh) << 23);
   const int k = __float2int_rn(a.lo * scale);
-  const long long db = __double_as_longlong(d);
-  const long long rb = db + (a.hi < 0.f ? -(long long)k : (long long)k);
-  if ((rb >> 52) != (db >> 52)) return d + (double)a.lo;
+  const long long rb = db + ((hb >> 31) ? -(long long)k : (long long)k);
+  if ((rb >> 52) != (db >> 52)) return df_add_rare(a.hi, a.lo);
   return __longlong_as_double(rb);
 }
 
