@@ -313,28 +313,25 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     ebe_ms = float(np.mean(per))
 
-    # e2e: host pinned x -> device, product, device -> host y, every step
+    # e2e: through fe_ebe_apply_host, every step copies its x from pinned host memory
+    # and its y back (consecutive calls overlap copy-in, product and copy-out)
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x)
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        M.ebe(xd, out=y)
-        yh.copy_(y, non_blocking=True)
+    for _ in range(3):
+        M.ebe_host(xh, out=yh)
     torch.cuda.synchronize()
     e_steps = max(5, args.steps // 5)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(e_steps):
-        xd.copy_(xh, non_blocking=True)
-        M.ebe(xd, out=y)
-        yh.copy_(y, non_blocking=True)
+        M.ebe_host(xh, out=yh)
     t1.record()
     torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1) / e_steps
     e2e = {"value": 3.0 * N * R * world / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF·cases/s",
-           "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4)}
+           "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(y.numel() * 4),
+           "api": "fe_ebe_apply_host (pinned host x and y, copies overlapped across calls)"}
 
     hbm, peak_src = load_peaks()
     flops = E * ebe_flops_per_element(R)

@@ -154,6 +154,24 @@ fe_status fe_mesh_set_log_young(fe_mesh* mesh, const double* logE_dev, void* str
 fe_status fe_ebe_apply(const fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x_dev, void* y_dev,
                        void* stream);
 
+/*
+ * fe_ebe_apply_host -- fe_ebe_apply with x and y in HOST memory: x_host is copied
+ * to the device, the product runs there, and y is copied back to y_host.
+ *   x_host, y_host  host [N][R][3] of dtype; page-locked memory (cudaHostAlloc,
+ *                   cudaHostRegister, torch pin_memory) lets the copies run
+ *                   asynchronously and overlap; pageable memory also works
+ * Stream-ordered and asynchronous: the call returns once the work is queued.
+ * x_host must hold the input when the call is made and must not change, and
+ * y_host must not be read, until `stream` reaches the end of the call
+ * (synchronise it). The copy-in does not wait for work queued earlier on
+ * `stream`. The library keeps two device buffer sets and its own copy and
+ * compute streams with the mesh, used by alternate calls, so that consecutive
+ * calls overlap the copy-in of one, the product of the previous one and the
+ * copy-out of the one before (the host<->device link and the GPU work in
+ * parallel). Not safe for concurrent calls on the same mesh from several threads.
+ */
+fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void* x_host, void* y_host, void* stream);
+
 /* EBE kernel variants (all compute fe_ebe_apply's result):
  *   FE_EBE_DIRECT  one thread per (element, case), inputs gathered from global
  *                  memory, results added with global atomics (the paper's GPU
@@ -352,6 +370,11 @@ fe_status fe_coarse_block_jacobi(const fe_mesh* mesh, double* binv4_dev, void* s
  * int32 [N4], may be NULL) the aggregate of each coarse node. Synchronous. Fails
  * with FE_EINVAL if the coarse matrices do not fit in a quarter of free memory. */
 fe_status fe_level2_info(const fe_mesh* mesh, int64_t* n_agg, int32_t* agg_host, void* stream);
+
+/* fe_coarse_matrix_info -- builds the assembled coarse matrices if needed (as
+ * fe_level2_info) and returns their block counts: *n_blocks1 of K1_bc, *n_blocks2
+ * of A2 (either may be NULL). Synchronous. */
+fe_status fe_coarse_matrix_info(const fe_mesh* mesh, int64_t* n_blocks1, int64_t* n_blocks2, void* stream);
 
 /* fe_level2_apply -- y2 = A2 x2, R cases, device float [NA][R][3], not aliased. */
 fe_status fe_level2_apply(const fe_mesh* mesh, int32_t R, const float* x2, float* y2, void* stream);

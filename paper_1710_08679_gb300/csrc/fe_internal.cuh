@@ -163,6 +163,22 @@ struct Coarse {
   DevBuf binv2_64, binv2_32;  // [NA][9] inverse diagonal blocks of A2
 };
 
+// Products with host-resident vectors (fe_ebe_apply_host): two device buffer
+// sets used alternately and three streams, so that the copy-in of one call, the
+// product of the previous one and the copy-out of the one before overlap.
+struct HostPipe {
+  int R = 0;
+  int dtype = -1;
+  DevBuf x[2], y[2];
+  cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+  cudaEvent_t h2d[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr};
+  int next = 0;
+  HostPipe() = default;
+  HostPipe(const HostPipe&) = delete;
+  HostPipe& operator=(const HostPipe&) = delete;
+  ~HostPipe();
+};
+
 struct SolverWork;  // defined in fe_solver.cu
 
 }  // namespace fe
@@ -203,6 +219,8 @@ struct fe_mesh {
   fe::Coarse coarse;
   // solver workspace (allocated lazily per R)
   fe::SolverWork* work = nullptr;
+  // buffers and streams of products with host vectors (allocated on first use)
+  std::unique_ptr<fe::HostPipe> host_pipe;
 
   template <typename T>
   fe::MeshView<T> view() const;

@@ -33,7 +33,8 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
             "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
-            "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info"]
+            "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info",
+            "fe_ebe_apply_host"]
 
 
 class FeError(RuntimeError):
@@ -101,12 +102,13 @@ def load(path: Optional[str] = None):
         getattr(lib, name).argtypes = [_vp, _i32, _vp, _vp, _vp]
     lib.fe_level2_block_jacobi.argtypes = [_vp, _vp, _vp]
     lib.fe_coarse_matrix_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]
+    lib.fe_ebe_apply_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
                  "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
                  "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
-                 "fe_level2_block_jacobi", "fe_coarse_matrix_info"):
+                 "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -210,6 +212,25 @@ class Mesh:
         y = torch.empty_like(x) if out is None else out
         yp = _dev_ptr(y, x.dtype, x.shape, name="out")
         _check(load().fe_ebe_apply(self._h, R, dt, xp, yp, self._stream()), "fe_ebe_apply")
+        return y
+
+    def ebe_host(self, x, out=None):
+        """y = K_bc x for host tensors x [N, R, 3] (float64 or float32; pinned memory
+        lets consecutive calls overlap copies and products). Asynchronous on the
+        current stream: synchronise it before reading the result or changing x."""
+        torch = _torch()
+        if not isinstance(x, torch.Tensor) or x.is_cuda or not x.is_contiguous():
+            raise TypeError("x must be a contiguous CPU tensor")
+        if x.dim() != 3 or x.shape[0] != self.n_nodes or x.shape[2] != 3:
+            raise ValueError("x must be [N, R, 3]")
+        dt = {torch.float64: FE_F64, torch.float32: FE_F32}.get(x.dtype)
+        if dt is None:
+            raise TypeError("x must be float64 or float32")
+        y = torch.empty_like(x) if out is None else out
+        if y.is_cuda or not y.is_contiguous() or y.shape != x.shape or y.dtype != x.dtype:
+            raise ValueError("out must be a contiguous CPU tensor like x")
+        _check(load().fe_ebe_apply_host(self._h, int(x.shape[1]), dt, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(y.data_ptr()), self._stream()), "fe_ebe_apply_host")
         return y
 
     def set_variant(self, R: int, dtype, variant: int, tile_elems: int = 48):

@@ -198,3 +198,25 @@ def test_full_size_crust_block_sampled_rows(dtype):
     assert rel_l2(y[nodes], ys) <= (TOL64 if dtype == "f64" else TOL32)
     if dtype == "f64":
         assert rel_l2(y2[nodes], ys) <= TOL64
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_products_pipeline_across_calls(dtype, pinned):
+    """fe_ebe_apply_host: three calls in a row with different host inputs (the
+    copies of consecutive calls overlap) each give the oracle's product."""
+    m = MESHES["ragged"]()
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    xs = [torch.from_numpy(mg.random_vectors(m.n_nodes, 4, seed=80 + k)).to(tdt) for k in range(3)]
+    if pinned:
+        xs = [x.pin_memory() for x in xs]
+    ys = [torch.empty_like(x).pin_memory() if pinned else torch.empty_like(x) for x in xs]
+    for x, y in zip(xs, ys):
+        M.ebe_host(x, out=y)
+    torch.cuda.synchronize()
+    for x, y in zip(xs, ys):
+        ref = oracle.spmv(K, x.double().numpy())
+        assert rel_l2(y.double().numpy(), ref) <= (TOL32 if dtype == "f32" else TOL64)
