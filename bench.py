@@ -453,6 +453,17 @@ def run_solves(m, iface, M, torch, fe, world, profile="uniform",
     t_amg = time.perf_counter() - t0
     du3 = float(torch.linalg.norm(u3 - u) / torch.linalg.norm(u))
     amg_rate = R / t_amg
+    # the paper tuned its inner-loop settings (its table: 0.1/30, 0.05/300) for
+    # its machines; on GB300 an outer iteration's FP64 product is dear relative to
+    # FP32 inner work, and tighter inner loops (fewer outer iterations) pay
+    loops = dict(eps_inner=0.01, n_inner=100, eps_inner1=0.01, n_inner1=500)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u4, stats4, st4 = M.solve(f, solver="fcg_mg", tol=1e-8, raise_on_fail=False, **loops)
+    torch.cuda.synchronize()
+    t_tuned = time.perf_counter() - t0
+    du4 = float(torch.linalg.norm(u4 - u) / torch.linalg.norm(u))
+    tuned_rate = R / t_tuned
     return {"workload": workload,
             "mixed_fcg": {"case_solves_per_s": mixed_rate * world, "seconds": t_mixed, "all_converged": ok,
                           "outer": [s["outer"] for s in stats], "inner": [s["inner"] for s in stats],
@@ -474,8 +485,16 @@ def run_solves(m, iface, M, torch, fe, world, profile="uniform",
                                      "iters": [s["outer"] for s in plain_stats],
                                      "relres": [s["relres"] for s in plain_stats],
                                      "rel_diff_vs_mixed": [s["rel_diff_vs_mixed"] for s in plain_stats]},
+            "mixed_fcg_two_level_gb300_loops": {"case_solves_per_s": tuned_rate * world, "seconds": t_tuned,
+                                                "loops": loops,
+                                                "all_converged": all(s["relres"] <= 1e-8 for s in stats4),
+                                                "outer": [s["outer"] for s in stats4],
+                                                "inner0": [s["inner"] for s in stats4],
+                                                "inner1": [s["inner1"] for s in stats4],
+                                                "relres_max": max(s["relres"] for s in stats4), "status": int(st4),
+                                                "rel_diff_vs_one_level": du4},
             "speedup": mixed_rate / plain_rate, "speedup_two_level": mg_rate / plain_rate,
-            "speedup_three_level": amg_rate / plain_rate}
+            "speedup_three_level": amg_rate / plain_rate, "speedup_two_level_gb300_loops": tuned_rate / plain_rate}
 
 
 def run_many(args):
