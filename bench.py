@@ -48,11 +48,13 @@ def parse():
                     help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
-    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer", "coarse"],
+    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer", "coarse", "solve"],
                     help="ebe: the EBE line on the 70x70x35 crust block (default); many: 96 unit-slip cases on "
                          "the 120x120x60 block through fe_solve_many vs the plain FP64 PCG one case at a time")
     ap.add_argument("--many-cases", type=int, default=96, help="cases of --workload many")
     ap.add_argument("--many-plain", type=int, default=1, help="cases timed with the plain FP64 PCG")
+    ap.add_argument("--solver", choices=["pcg64", "fcg_mixed", "fcg_mg", "fcg_amg"], default="fcg_mg",
+                    help="solver of --workload solve")
     ap.add_argument("--many-solver", choices=["fcg_mixed", "fcg_mg", "fcg_amg"], default="fcg_mixed",
                     help="many-case solver: inner loop at level 0 only, with the TET4 level 1 first, or with "
                          "levels 2 and 1 first")
@@ -588,6 +590,41 @@ def run_two_layer(args):
     print(json.dumps(out), flush=True)
 
 
+def run_one_solve(args):
+    """One batched solve of the 16 slip patches on the 70x70x35 crust block with
+    --solver, after all set-up (kernel tuning, coarse levels, one untimed solve),
+    inside the NVTX range "timed_solve" (so a profiler can be limited to it)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08679_gb300 import fe
+    from paper_1710_08679_gb300 import meshgen as mg
+    shape = SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x"))
+    m, iface = make_workload(shape)
+    M = fe.Mesh.from_mesh(m)
+    R = R_MAIN
+    f = slip_rhs(m, iface, R, M, torch, fe)
+    M.tune(R, "f32")
+    M.tune(R, "f64")
+    M.tune(1, "f64")
+    if args.solver in ("fcg_mg", "fcg_amg"):
+        M.coarse_block_jacobi()
+        M.coarse_matrix_info()
+    M.solve(f, solver=args.solver, tol=1e-8, raise_on_fail=False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_solve")
+    t0 = time.perf_counter()
+    u, stats, st = M.solve(f, solver=args.solver, tol=1e-8, raise_on_fail=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"workload": "crust_%dx%dx%d_tet10 16 unit-slip patches" % shape, "solver": args.solver,
+                      "seconds": dt, "case_solves_per_s": R / dt, "status": int(st),
+                      "outer": [s["outer"] for s in stats], "inner0": [s["inner"] for s in stats],
+                      "inner1": [s["inner1"] for s in stats], "inner2": [s["inner2"] for s in stats],
+                      "relres_max": max(s["relres"] for s in stats)}), flush=True)
+
+
 def run_coarse(args):
     """The level-1 (TET4) and level-2 (aggregation) operators at R = 16, FP32, on
     the 70x70x35 crust block: assembled K1_bc product, TET4 element-by-element
@@ -650,6 +687,8 @@ def main():
         run_two_layer(args)
     elif args.workload == "coarse":
         run_coarse(args)
+    elif args.workload == "solve":
+        run_one_solve(args)
     else:
         run_ours(args)
 
