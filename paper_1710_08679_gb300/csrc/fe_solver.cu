@@ -68,6 +68,7 @@ struct SolverWork {
   DevBuf rb1, ub1, eb1, pb1, qb1; // float  [N4][R][3] (level 1, allocated when used)
   DevBuf rb2, ub2, eb2, pb2, qb2; // float  [NA][R][3] (level 2, allocated when used)
   DevBuf tu, tq;                  // double [N][3] (single-case true residual)
+  DevBuf tall;                    // double [N][R][3] (true residuals of several cases at once, lazily)
   DevBuf d, i;                    // case state
   cudaStream_t stream = nullptr;
   cudaStream_t body = nullptr;    // records the bodies of the graph's inner-loop nodes
@@ -507,6 +508,25 @@ __global__ void k_outer_update(int64_t N, Cases C, double* __restrict__ rv, cons
   }
   VEC_LOOP_END
   reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RN2 * C.R);
+}
+
+// true residuals of the candidate cases from one all-case product t = K u:
+// r_c = P f_c - t_c written for them, rt2[c] += ||r_c||^2
+__global__ void k_cand_resid(int64_t N, Cases C, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
+                             const double* __restrict__ t, double* __restrict__ rv) {
+  extern __shared__ double sm[];
+  double acc = 0.0;
+  VEC_LOOP_BEGIN
+  if (C.I(I_CAND, r)) {
+    const int mk = nmask[n];
+    for (int c = 0; c < 3; ++c) {
+      const double v = ((mk >> c) & 1) ? f[o + c] - t[o + c] : 0.0;
+      rv[o + c] = v;
+      acc += v * v;
+    }
+  }
+  VEC_LOOP_END
+  reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_RT2 * C.R);
 }
 
 // single-case helpers for the true-residual confirmation
@@ -1150,12 +1170,26 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
       FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
       FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
       FE_CUDA(cudaStreamSynchronize(s));
-      // confirm candidates with the true FP64 residual
+      // confirm candidates with the true FP64 residual: one all-case product when
+      // a quarter or more of the cases are candidates, else one product per case
       bool any_active = false;
+      int n_cand = 0;
+      for (int c = 0; c < R; ++c) n_cand += hi[I_CAND * R + c] ? 1 : 0;
+      const bool batched = R > 1 && 4 * n_cand >= R;
+      if (batched) {
+        if (!w->tall.ptr) w->tall.alloc((size_t)S.N * R * 3 * sizeof(double));
+        ebe_apply<double>(m, R, u, w->tall.as<double>(), s);
+        FE_CUDA(cudaMemsetAsync(w->d.as<double>() + D_RT2 * R, 0, R * sizeof(double), s));
+        S.vec(k_cand_resid, m->nmask.as<uint8_t>(), f, (const double*)w->tall.as<double>(), w->r.as<double>());
+        FE_CUDA(cudaMemcpyAsync(hd.data() + D_RT2 * R, w->d.as<double>() + D_RT2 * R, R * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaStreamSynchronize(s));
+      }
       for (int c = 0; c < R; ++c) {
         if (hi[I_CAND * R + c]) {
           const double fn2 = hd[D_FN2 * R + c];
-          const double rel = S.true_relres(c, fn2, true);
+          const double rel = batched ? (fn2 > 0.0 ? std::sqrt(hd[D_RT2 * R + c] / fn2) : 0.0)
+                                     : S.true_relres(c, fn2, true);
           int one = 1, zero = 0;
           FE_CUDA(cudaMemcpyAsync(w->i.as<int>() + I_CAND * R + c, &zero, 4, cudaMemcpyHostToDevice, s));
           if (rel <= o.tol) {
