@@ -19,6 +19,7 @@
 
 #include "fe_df.cuh"
 #include "fe_element.cuh"
+#include "fe_element_df.cuh"
 #include "fe_internal.cuh"
 
 namespace fe {
