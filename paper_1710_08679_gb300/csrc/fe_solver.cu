@@ -1343,8 +1343,10 @@ namespace fe {
 static int choose_slots(const fe_mesh* m, int n_cases) {
   size_t free_b = 0, total_b = 0;
   FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  // per slot: FP64 F, U, r, p, q and FP32 rbar, ubar, e, pbar, qbar vectors of [N][3]
-  const double per_slot = (double)m->n_nodes * 3 * (5 * 8 + 5 * 4);
+  // per slot: FP64 F, U, r, p, q and the all-case true-residual product, FP32
+  // rbar, ubar, e, pbar, qbar vectors of [N][3] (the coarse levels' vectors are
+  // a tenth of that and the float-float geometry E x 128 B, inside the margin)
+  const double per_slot = (double)m->n_nodes * 3 * (6 * 8 + 5 * 4);
   const double budget = 0.7 * (double)free_b;
   int R = 32;
   while (R > 1 && (R > n_cases || R * per_slot > budget)) R /= 2;

@@ -220,3 +220,33 @@ def test_host_buffer_products_pipeline_across_calls(dtype, pinned):
     for x, y in zip(xs, ys):
         ref = oracle.spmv(K, x.double().numpy())
         assert rel_l2(y.double().numpy(), ref) <= (TOL32 if dtype == "f32" else TOL64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_largest_case_count_R64(dtype):
+    """R = 64, the largest batch the ABI accepts (the tuned choice among the
+    kernels compiled for it), against the oracle."""
+    m = MESHES["ragged"]()
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, 64, seed=64)
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    M.tune(64, dtype)
+    y = run(M, x, torch.float32 if dtype == "f32" else torch.float64)
+    assert rel_l2(y, oracle.spmv(K, x)) <= (TOL32 if dtype == "f32" else TOL64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_fully_constrained_mesh_is_identity(variant):
+    """Every DOF fixed: K_bc = I, so every kernel must return x exactly."""
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    m = MESHES["box2"]()
+    M = fe.Mesh(m.coords, m.conn, m.young, m.poisson, np.zeros_like(m.free))
+    for dtype in (torch.float64, torch.float32):
+        x = torch.from_numpy(mg.random_vectors(m.n_nodes, 4, seed=9)).to(dtype)
+        y = run(M, x.numpy().astype(np.float64), dtype, variant, tile=8)
+        assert np.array_equal(y, x.double().numpy())

@@ -203,3 +203,29 @@ def test_solve_many_streams_cases_through_slots(box8, solver, R_slots):
             continue
         assert stats[c]["status"] == 0 and stats[c]["relres"] <= 1e-8, (c, stats[c])
         assert rel_l2(u[c], ud[:, c]) <= 1e-6, c
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solver", ["pcg64", "fcg_mixed", "fcg_mg"])
+def test_all_zero_batch_returns_at_once(box8, solver):
+    """Every right-hand side zero: u = 0 for every case, no iteration."""
+    m, K, M = box8
+    f = np.zeros((m.n_nodes, 5, 3))
+    u, stats, st = M.solve(cuda(f), u0=cuda(np.ones((m.n_nodes, 5, 3))), solver=solver, tol=1e-8)
+    assert st == 0
+    assert np.all(u.cpu().numpy() == 0.0)
+    assert all(s["outer"] == 0 and s["relres"] == 0.0 for s in stats)
+
+
+@pytest.mark.gpu
+def test_64_cases_in_one_batch(box8):
+    """R = 64 cases at once through the two-level solver (the ABI's largest R)."""
+    m, K, M = box8
+    rng = np.random.default_rng(64)
+    F = rng.standard_normal((m.n_nodes, 64, 3)) * 1e9 * m.free[:, None, :]
+    u, stats, st = M.solve(cuda(F), solver="fcg_mg", tol=1e-8)
+    assert st == 0
+    ud = oracle.direct_solve(K, F)
+    for r in range(64):
+        assert stats[r]["relres"] <= 1e-8
+        assert rel_l2(u.cpu().numpy()[:, r], ud[:, r]) <= 1e-6
