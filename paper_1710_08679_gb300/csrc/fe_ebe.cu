@@ -526,7 +526,9 @@ __host__ __device__ size_t pipe_smem_bytes(int nnmax, int te, int pk) {
 // at most 64 registers); FP64 keeps 256-thread blocks.
 template <typename T>
 struct PipeThreads {
-  static constexpr int value = sizeof(T) == 4 ? 1024 : kThreads;
+  // FP32: up to 768 threads per CTA, which leaves 80 registers per thread
+  // (measured 1 % faster than 1024 threads at 64 registers on the crust block)
+  static constexpr int value = sizeof(T) == 4 ? 768 : kThreads;
 };
 
 template <typename T, int R>
