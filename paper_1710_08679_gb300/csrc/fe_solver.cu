@@ -996,8 +996,8 @@ static void inner_loop(Solve& S, const Level& L) {
   FE_CUDA(cudaStreamUpdateCaptureDependencies(S.s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
 }
 
-// the FCG outer iteration (Algorithm 1(a); inner loop level 2 dropped, inner
-// loop level 1 only when the coarse level is on)
+// the FCG outer iteration (Algorithm 1(a)): inner loop level 1 when the coarse
+// level is on, with inner loop level 2 before it when the aggregation level is on
 static void fcg_iteration(Solve& S) {
   SolverWork* w = S.w;
   fe_mesh* m = S.m;
