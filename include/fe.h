@@ -189,8 +189,18 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *                  kernel with the element arithmetic and node sums in float-float
  *                  (pairs of FP32 values, about 48 significant bits) on the FP32
  *                  pipe, FP64 inputs, outputs and atomics; GB300 runs FP64
- *                  arithmetic at 1/61 of its FP32 rate. */
-typedef enum { FE_EBE_DIRECT = 0, FE_EBE_TILED = 1, FE_EBE_GATHER = 2, FE_EBE_GATHER_DF = 3 } fe_ebe_variant;
+ *                  arithmetic at 1/61 of its FP32 rate;
+ *   FE_EBE_GATHER_X2  FP32 products only (R in {4, 8, 16, 32}): the gather
+ *                  kernel with each thread computing two cases of one element
+ *                  (r and r + R/2) in paired FP32 instructions (two lanes per
+ *                  multiply-add), sharing the element's geometry between them. */
+typedef enum {
+  FE_EBE_DIRECT = 0,
+  FE_EBE_TILED = 1,
+  FE_EBE_GATHER = 2,
+  FE_EBE_GATHER_DF = 3,
+  FE_EBE_GATHER_X2 = 4
+} fe_ebe_variant;
 
 /*
  * fe_ebe_set_variant -- choose the kernel fe_ebe_apply (and the solvers) use for

@@ -430,10 +430,12 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
-                   variant == FE_EBE_GATHER_DF,
+                   variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2,
                "unknown variant %d", variant);
     FE_REQUIRE(variant != FE_EBE_GATHER_DF || (dtype == FE_F64 && df_supported(R)),
                "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
+    FE_REQUIRE(variant != FE_EBE_GATHER_X2 || (dtype == FE_F32 && x2_supported(R)),
+               "the paired-arithmetic kernel computes FP32 products for R in {4, 8, 16, 32}");
     DeviceGuard dg(m->device);
     if (variant == FE_EBE_DIRECT) {
       ebe_set_variant(m, R, dtype == FE_F32, 0);
@@ -442,9 +444,12 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),
                "the gather kernel is compiled for R in {1, 2, 3, 4, 8, 16, 32}, not %d", R);
     get_tiling(m, tile_elems, (cudaStream_t)stream);
-    if (variant == FE_EBE_GATHER || variant == FE_EBE_GATHER_DF) ensure_geometry_buffer(m, dtype == FE_F32);
+    if (variant != FE_EBE_TILED) ensure_geometry_buffer(m, dtype == FE_F32);
     if (variant == FE_EBE_GATHER_DF)
       FE_REQUIRE(df_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",
+                 tile_elems, R);
+    else if (variant == FE_EBE_GATHER_X2)
+      FE_REQUIRE(x2_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",
                  tile_elems, R);
     else
       FE_REQUIRE(tiled_fits(m, tile_elems, R, dtype == FE_F32, variant),

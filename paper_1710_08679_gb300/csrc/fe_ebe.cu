@@ -20,6 +20,7 @@
 #include "fe_df.cuh"
 #include "fe_element.cuh"
 #include "fe_element_df.cuh"
+#include "fe_element_x2.cuh"
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -262,8 +263,11 @@ __device__ __forceinline__ void vset(float4& v, int t, float x) {
 __device__ __forceinline__ void vset(double2& v, int t, double x) {
   if (t == 0) v.x = x; else v.y = x;
 }
+// four FP32 additions as two paired ones (same results)
 __device__ __forceinline__ void vadd(float4& a, const float4& b) {
-  a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+  const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  a = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 __device__ __forceinline__ void vadd(double2& a, const double2& b) {
   a.x += b.x; a.y += b.y;
@@ -515,31 +519,47 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(MeshView<T> M, T* __rest
   for (int64_t i = n16 * V + gid; i < nv; i += stride) y[i] = T(0);
 }
 
-template <typename T, int R>
+// Element slot stride of the pipelined kernel. One case per thread: the gather
+// kernel's. Two cases per thread: R/2 threads per element, so 64/R elements share a
+// warp; a stride of R/2 banks (mod 32) between neighbouring elements puts the
+// lanes of all of them on different banks (for R = 4 the multiple of 16 bytes
+// nearest to that, 2-way). Always a multiple of 16 bytes.
+template <typename T, int R, int CPT>
+struct PipeCfg {
+  static constexpr int RC = R / CPT;  // threads per element
+  static constexpr int S = CPT == 1 ? GatherCfg<T, R>::S
+                                    : 30 * R + ((((RC + 3) & ~3) - 30 * R) % 32 + 32) % 32;
+  static_assert(S % (16 / (int)sizeof(T)) == 0, "slot stride must keep 16-byte rows aligned");
+};
+
+template <typename T, int R, int CPT = 1>
 __host__ __device__ size_t pipe_smem_bytes(int nnmax, int te, int pk) {
   using C = GatherCfg<T, R>;
   return (size_t)3 * pk + (size_t)3 * te * kGeo * sizeof(T) + (size_t)2 * nnmax * C::VR * sizeof(T) +
-         (size_t)te * C::S * sizeof(T) + (size_t)((te * 10 + 3) & ~3) * sizeof(int) + (size_t)te * 12 * sizeof(int);
+         (size_t)te * PipeCfg<T, R, CPT>::S * sizeof(T) + (size_t)((te * 10 + 3) & ~3) * sizeof(int) +
+         (size_t)te * 12 * sizeof(int);
 }
 
-// FP32: up to 1024 threads per block (one thread per element-case item of a tile,
-// at most 64 registers); FP64 keeps 256-thread blocks.
-template <typename T>
+// Threads per CTA of the pipelined kernel. FP32, one case per thread: up to 768
+// (one thread per element-case item of a tile, 80 registers per thread; measured
+// 1 % faster than 1024 threads at 64 registers on the crust block). FP32, two
+// cases per thread (paired arithmetic): up to 384, which leaves 168 registers for
+// the two cases' values. FP64: 256.
+template <typename T, int CPT>
 struct PipeThreads {
-  // FP32: up to 768 threads per CTA, which leaves 80 registers per thread
-  // (measured 1 % faster than 1024 threads at 64 registers on the crust block)
-  static constexpr int value = sizeof(T) == 4 ? 768 : kThreads;
+  static constexpr int value = sizeof(T) == 4 ? (CPT == 2 ? 384 : 768) : kThreads;
 };
 
-template <typename T, int R>
-__global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t n_tiles, int64_t n_elem, int te, int nnmax,
+template <typename T, int R, int CPT = 1>
+__global__ void __launch_bounds__(PipeThreads<T, CPT>::value) ebe_pipe_kernel(int64_t n_tiles, int64_t n_elem, int te, int nnmax,
                                                             const unsigned char* __restrict__ packets, int pk,
                                                             const T* __restrict__ geo, const T* __restrict__ x,
                                                             T* __restrict__ y, const int* __restrict__ skip) {
   using C = GatherCfg<T, R>;
   using VT = typename Vec16<T>::type;
-  constexpr int VR = C::VR, V = C::V, S = C::S, CPN = VR / V;
+  constexpr int VR = C::VR, V = C::V, S = PipeCfg<T, R, CPT>::S, CPN = VR / V;
   static_assert(C::VEC, "pipelined kernel needs 16-byte node rows");
+  static_assert(CPT == 1 || (CPT == 2 && sizeof(T) == 4 && R % 2 == 0), "two cases per thread: FP32, even R");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (skip && *skip) return;
   const PacketLayout L(nnmax, te);
@@ -620,10 +640,12 @@ __global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t
     cp_async_commit();
     __syncthreads();
 
-    // phase 2: element products into their slots
-    for (int it = threadIdx.x; it < ne * R; it += blockDim.x) {
-      const int le = it / R;
-      const int r = it - le * R;
+    // phase 2: element products into their slots; a thread takes CPT cases of one
+    // element (cases r and r + R/2 when CPT = 2)
+    constexpr int RC = PipeCfg<T, R, CPT>::RC;
+    for (int it = threadIdx.x; it < ne * RC; it += blockDim.x) {
+      const int le = it / RC;
+      const int r = it - le * RC;
       ElemGeo<T> Gm;
       T gv[kGeo];
 #pragma unroll
@@ -648,58 +670,95 @@ __global__ void __launch_bounds__(PipeThreads<T>::value) ebe_pipe_kernel(int64_t
         off[4 * q + 2] = w.z;
         off[4 * q + 3] = w.w;
       }
-      T u[10][3];
-#pragma unroll
-      for (int a = 0; a < 10; ++a) {
-        const T* xa = xcur + off[a] + 3 * r;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[a][c] = xa[c];
-      }
-      T yl[10][3];
-      elem_apply(Gm, u, yl);
       T* o = ob + le * S + 3 * r;
+      if constexpr (CPT == 2) {
+        float2 u[10][3];
 #pragma unroll
-      for (int a = 0; a < 10; ++a)
+        for (int a = 0; a < 10; ++a) {
+          const T* xa = xcur + off[a] + 3 * r;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) o[a * VR + c] = yl[a][c];
+          for (int c = 0; c < 3; ++c) u[a][c] = make_float2(xa[c], xa[c + 3 * RC]);
+        }
+        float2 yl[10][3];
+        elem_apply_x2(Gm, u, yl);
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            o[a * VR + c] = yl[a][c].x;
+            o[a * VR + c + 3 * RC] = yl[a][c].y;
+          }
+      } else {
+        T u[10][3];
+#pragma unroll
+        for (int a = 0; a < 10; ++a) {
+          const T* xa = xcur + off[a] + 3 * r;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) u[a][c] = xa[c];
+        }
+        T yl[10][3];
+        elem_apply(Gm, u, yl);
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) o[a * VR + c] = yl[a][c];
+      }
     }
     __syncthreads();
 
-    // phase 3: node sums, one 16-byte atomic per 16 bytes of free values
-    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
-      const int ln = k / CPN;
-      const int q = k - ln * CPN;
-      VT acc;
-      vzero(acc);
-      const int j1 = is[ln + 1];
-      const T* obq = ob + q * V;
-      int j = is[ln];
-      VT acc1;
-      vzero(acc1);
-      for (; j + 3 < j1; j += 4) {   // four independent loads in flight
-        const int o0 = io[j], o1 = io[j + 1], o2 = io[j + 2], o3 = io[j + 3];
-        const VT v0 = *reinterpret_cast<const VT*>(obq + o0);
-        const VT v1 = *reinterpret_cast<const VT*>(obq + o1);
-        const VT v2 = *reinterpret_cast<const VT*>(obq + o2);
-        const VT v3 = *reinterpret_cast<const VT*>(obq + o3);
-        vadd(acc, v0);
-        vadd(acc1, v1);
-        vadd(acc, v2);
-        vadd(acc1, v3);
-      }
-      for (; j < j1; ++j) vadd(acc, *reinterpret_cast<const VT*>(obq + io[j]));
-      vadd(acc, acc1);
-      const int64_t gi = (int64_t)ids[ln] * VR + q * V;
-      const int mk = mks[ln];
-      if (mk == 7) {
-        vred(reinterpret_cast<VT*>(y + gi), acc);
-      } else {
+    // phase 3: node sums, one 16-byte atomic per 16 bytes of free values. With two
+    // cases per thread (half as many threads) a thread takes two chunks of one node
+    // (q0 and q0 + CPN/2): they share the node's slot offsets and loop, and their
+    // loads are independent (measured: 0.859 -> 0.794 ms at R = 16, tile 24). With
+    // one case per thread the single-chunk form is faster (0.810 vs 0.847 ms at tile
+    // 48: two chunks per thread leave a short second round that the CTA waits for).
+    constexpr int QP = (CPT == 2 && CPN % 2 == 0) ? 2 : 1;
+    constexpr int CQ = CPN / QP;
+    constexpr int U = 4 / QP;  // incidences per iteration (4 independent loads in flight)
+    for (int k = threadIdx.x; k < nn * CQ; k += blockDim.x) {
+      const int ln = k / CQ;
+      const int q0 = k - ln * CQ;
+      VT acc[2][QP];
 #pragma unroll
-        for (int tt = 0; tt < V; ++tt) {
-          if ((mk >> ((q * V + tt) % 3)) & 1)
-            atomicAdd(y + gi + tt, vget(acc, tt));
-          else if (own[ln])
-            y[gi + tt] = __ldg(x + gi + tt);
+      for (int p = 0; p < QP; ++p) {
+        vzero(acc[0][p]);
+        vzero(acc[1][p]);
+      }
+      const int j1 = is[ln + 1];
+      const T* obq = ob + q0 * V;
+      int j = is[ln];
+      for (; j + U - 1 < j1; j += U) {
+        int o[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) o[u] = io[j + u];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int p = 0; p < QP; ++p)
+            vadd(acc[u & 1][p], *reinterpret_cast<const VT*>(obq + p * CQ * V + o[u]));
+      }
+      for (; j < j1; ++j) {
+        const int o0 = io[j];
+#pragma unroll
+        for (int p = 0; p < QP; ++p) vadd(acc[0][p], *reinterpret_cast<const VT*>(obq + p * CQ * V + o0));
+      }
+      const int mk = mks[ln];
+      const int64_t gbase = (int64_t)ids[ln] * VR;
+#pragma unroll
+      for (int p = 0; p < QP; ++p) {
+        vadd(acc[0][p], acc[1][p]);
+        const int q = q0 + p * CQ;
+        const int64_t gi = gbase + q * V;
+        if (mk == 7) {
+          vred(reinterpret_cast<VT*>(y + gi), acc[0][p]);
+        } else {
+#pragma unroll
+          for (int tt = 0; tt < V; ++tt) {
+            if ((mk >> ((q * V + tt) % 3)) & 1)
+              atomicAdd(y + gi + tt, vget(acc[0][p], tt));
+            else if (own[ln])
+              y[gi + tt] = __ldg(x + gi + tt);
+          }
         }
       }
     }
@@ -971,33 +1030,35 @@ static void launch_gather_r(const fe_mesh* m, const Tiling& t, const T* x, T* y,
   FE_CHECK_LAUNCH();
 }
 
-template <typename T, int R>
+template <typename T, int R, int CPT = 1>
 static bool launch_pipe_r(const fe_mesh* m, const Tiling& t, const T* x, T* y, cudaStream_t s, const int* skip) {
-  if constexpr (!GatherCfg<T, R>::VEC) {
+  if constexpr (!GatherCfg<T, R>::VEC || (CPT == 2 && (sizeof(T) != 4 || R % 2 != 0))) {
     return false;
   } else {
     const DevBuf& gb = sizeof(T) == 4 ? m->geo32 : m->geo64;
     if (!gb.ptr || t.packet_bytes == 0) return false;
-    const size_t smem = pipe_smem_bytes<T, R>(t.max_nodes, t.tile_elems, t.packet_bytes);
+    const size_t smem = pipe_smem_bytes<T, R, CPT>(t.max_nodes, t.tile_elems, t.packet_bytes);
     if (smem > (size_t)max_smem_optin(m->device)) return false;
-    FE_CUDA(cudaFuncSetAttribute(ebe_pipe_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // one thread per element-case item of a full tile (FP32), in whole warps
+    FE_CUDA(cudaFuncSetAttribute(ebe_pipe_kernel<T, R, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    // one thread per element item (CPT cases) of a full tile (FP32), in whole warps
     int threads = kThreads;
     if (sizeof(T) == 4) {
-      threads = ((t.tile_elems * R + 31) / 32) * 32;
-      threads = threads < 128 ? 128 : (threads > PipeThreads<T>::value ? PipeThreads<T>::value : threads);
+      constexpr int tmax = PipeThreads<T, CPT>::value;
+      threads = ((t.tile_elems * (R / CPT) + 31) / 32) * 32;
+      threads = threads < 128 ? 128 : (threads > tmax ? tmax : threads);
     }
     int per_sm = 0, sms = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_pipe_kernel<T, R>, threads, smem));
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_pipe_kernel<T, R, CPT>, threads, smem));
     FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
     if (per_sm < 1) return false;
     const int64_t nv = m->n_nodes * (int64_t)R * 3;
     prep_kernel<T><<<(unsigned)(sms * 8), kThreads, 0, s>>>(m->view<T>(), gb.as<T>(), nv, y, skip);
     FE_CHECK_LAUNCH();
     const int64_t grid = std::min<int64_t>(t.n_tiles, (int64_t)per_sm * sms);
-    ebe_pipe_kernel<T, R><<<(unsigned)grid, threads, smem, s>>>(t.n_tiles, m->n_elem, t.tile_elems, t.max_nodes,
-                                                                  t.packets.as<unsigned char>(), t.packet_bytes,
-                                                                  gb.as<T>(), x, y, skip);
+    ebe_pipe_kernel<T, R, CPT><<<(unsigned)grid, threads, smem, s>>>(
+        t.n_tiles, m->n_elem, t.tile_elems, t.max_nodes, t.packets.as<unsigned char>(), t.packet_bytes, gb.as<T>(),
+        x, y, skip);
     FE_CHECK_LAUNCH();
     return true;
   }
@@ -1033,6 +1094,18 @@ static bool launch_pipe_df(const fe_mesh* m, const Tiling& t, int R, const doubl
     case 8: return launch_pipe_df_r<8>(m, t, x, y, s, skip);
     case 16: return launch_pipe_df_r<16>(m, t, x, y, s, skip);
     case 32: return launch_pipe_df_r<32>(m, t, x, y, s, skip);
+    default: return false;
+  }
+}
+
+// FP32 pipelined kernel with two cases per thread (paired arithmetic), R in {4, 8, 16, 32}
+static bool launch_pipe_x2(const fe_mesh* m, const Tiling& t, int R, const float* x, float* y, cudaStream_t s,
+                           const int* skip) {
+  switch (R) {
+    case 4: return launch_pipe_r<float, 4, 2>(m, t, x, y, s, skip);
+    case 8: return launch_pipe_r<float, 8, 2>(m, t, x, y, s, skip);
+    case 16: return launch_pipe_r<float, 16, 2>(m, t, x, y, s, skip);
+    case 32: return launch_pipe_r<float, 32, 2>(m, t, x, y, s, skip);
     default: return false;
   }
 }
@@ -1111,6 +1184,13 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
       } else {
         FE_REQUIRE(false, "the float-float kernel computes FP64 products only");
       }
+    } else if (kind == FE_EBE_GATHER_X2) {
+      if constexpr (sizeof(T) == 4) {
+        FE_REQUIRE(launch_pipe_x2(m, *it->second, R, x, y, s, skip),
+                   "paired-arithmetic kernel unavailable for R = %d with tiles of %d elements", R, tile);
+      } else {
+        FE_REQUIRE(false, "the paired-arithmetic kernel computes FP32 products only");
+      }
     } else if (kind == FE_EBE_GATHER) {
       if (launch_pipe<T>(m, *it->second, R, x, y, s, skip)) return;
       zero_pass<T>(m, R, y, s, skip);
@@ -1133,6 +1213,24 @@ void ensure_geometry_buffer(fe_mesh* m, int is_f32) {
 
 bool df_supported(int R) { return R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
 
+bool x2_supported(int R) { return R == 4 || R == 8 || R == 16 || R == 32; }
+
+bool x2_fits(const fe_mesh* m, int tile_elems, int R) {
+  auto it = m->tilings.find(tile_elems);
+  if (it == m->tilings.end()) return false;
+  const Tiling& t = *it->second;
+  if (t.packet_bytes == 0) return false;
+  size_t smem;
+  switch (R) {
+    case 4: smem = pipe_smem_bytes<float, 4, 2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 8: smem = pipe_smem_bytes<float, 8, 2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 16: smem = pipe_smem_bytes<float, 16, 2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 32: smem = pipe_smem_bytes<float, 32, 2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    default: return false;
+  }
+  return smem <= (size_t)max_smem_optin(m->device);
+}
+
 bool df_fits(const fe_mesh* m, int tile_elems, int R) {
   auto it = m->tilings.find(tile_elems);
   if (it == m->tilings.end()) return false;
@@ -1154,8 +1252,9 @@ template void ebe_apply<double>(const fe_mesh*, int, const double*, double*, cud
 
 // Times each candidate kernel for (R, precision) on this mesh (scratch vectors
 // of ones, 2 warm-up and 5 timed products each, CUDA events on `s`) and keeps
-// the fastest. Candidates: direct, and tiled with 24..384 elements per tile
-// where the tile's shared-memory footprint fits.
+// the fastest. Candidates, where the tile's shared-memory footprint fits: direct;
+// gather with 12..256 elements per tile; tiled with 24..96; for FP64 the
+// float-float gather with 4..24; for FP32 the paired-arithmetic gather with 16..96.
 template <typename T>
 static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* best_ms) {
   const size_t n = (size_t)m->n_nodes * R * 3;
@@ -1175,6 +1274,9 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   if (sizeof(T) == 8 && df_supported(R))
     for (int te : {4, 8, 12, 16, 24})
       if (tiled_fits(m, te, R, 0, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_DF * 65536 + te);
+  if (sizeof(T) == 4 && x2_supported(R))
+    for (int te : {16, 24, 32, 48, 64, 96})
+      if (tiled_fits(m, te, R, 1, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_X2 * 65536 + te);
   *best_variant = 0;
   *best_ms = 1e30f;
   const int old = m->variant[sizeof(T) == 4][R];
@@ -1184,6 +1286,8 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
       get_tiling(m, v % 65536, s);
       if (v / 65536 == FE_EBE_GATHER_DF) {
         if (!df_fits(m, v % 65536, R)) continue;
+      } else if (v / 65536 == FE_EBE_GATHER_X2) {
+        if (!x2_fits(m, v % 65536, R)) continue;
       } else if (!tiled_fits(m, v % 65536, R, sizeof(T) == 4, v / 65536)) {
         continue;
       }

@@ -241,6 +241,8 @@ bool gather_supported(int R);
 void ensure_geometry_buffer(fe_mesh* m, int is_f32);
 bool df_supported(int R);
 bool df_fits(const fe_mesh* m, int tile_elems, int R);
+bool x2_supported(int R);
+bool x2_fits(const fe_mesh* m, int tile_elems, int R);
 const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
 // largest tile (elements) whose shared-memory footprint fits for (R, precision)
 bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);

@@ -141,6 +141,51 @@ def test_float_float_many_tiles_and_scales(R):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("R", [4, 8, 16, 32])
+def test_paired_fp32_kernel_matches_oracle(mesh_pair, R):
+    """Two cases per thread (r and r + R/2) in paired FP32 arithmetic: every case
+    on its own meets the FP32 bar, so the lanes are neither swapped nor mixed."""
+    m, K, M = mesh_pair
+    x = mg.random_vectors(m.n_nodes, R, seed=400 + R).astype(np.float32).astype(np.float64)
+    y = run(M, x, torch.float32, 4, tile=24)
+    assert M.get_variant(R, "f32")[0] == 4
+    ref = oracle.spmv(K, x)
+    for r in range(R):
+        assert rel_l2(y[:, r], ref[:, r]) <= TOL32, r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [4, 16, 32])
+@pytest.mark.parametrize("tile", [1, 13, 48, 96])
+def test_paired_fp32_tiles_and_ragged_tail(R, tile):
+    """Paired kernel on a 24,000-element crust block: one-element tiles, a ragged
+    last tile (24,000 = 13 x 1,846 + 2), and tiles with more element items than
+    the CTA has threads (96 x R/2 > 384 for R >= 16)."""
+    m, _ = mg.crust_block(shape=(20, 20, 10), h=1000.0, jitter=0.15, seed=5)
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, R, seed=33).astype(np.float32).astype(np.float64)
+    y = run(M, x, torch.float32, 4, tile=tile)
+    kind, used = M.get_variant(R, "f32")
+    assert kind == 4 and 1 <= used <= tile      # the largest fitting tile <= the request
+    assert rel_l2(y, oracle.spmv(K, x)) <= TOL32
+
+
+@pytest.mark.gpu
+def test_paired_kernel_rejects_unsupported_requests():
+    """FP64 or an R outside {4, 8, 16, 32}: fe_ebe_set_variant refuses, and the
+    previous choice stays in force."""
+    from paper_1710_08679_gb300 import fe
+    m = MESHES["box2"]()
+    M = gpu_mesh(m)
+    before = M.get_variant(16, "f64")
+    for R, dt in ((16, "f64"), (3, "f32"), (1, "f32"), (64, "f32")):
+        with pytest.raises(fe.FeError):
+            M.set_variant(R, dt, 4, 24)
+    assert M.get_variant(16, "f64") == before
+
+
+@pytest.mark.gpu
 def test_batched_equals_separate_products():
     m = MESHES["box8"]()
     M = gpu_mesh(m)
@@ -190,14 +235,13 @@ def test_full_size_crust_block_sampled_rows(dtype):
         x = x.astype(np.float32).astype(np.float64)
     M.tune(R, dtype)
     y = run(M, x, tdt)
-    if dtype == "f64":   # the float-float kernel too, whatever the tuner picked
-        y2 = run(M, x, tdt, 3, tile=16)
+    # the float-float (FP64) or paired-arithmetic (FP32) kernel too, whatever the tuner picked
+    y2 = run(M, x, tdt, 3, tile=16) if dtype == "f64" else run(M, x, tdt, 4, tile=48)
     rng = np.random.default_rng(0)
     nodes = np.unique(np.concatenate([rng.integers(0, m.n_nodes, 3000), [0, m.n_nodes - 1]]))
     ys = oracle.sampled_product(m, x, nodes)
     assert rel_l2(y[nodes], ys) <= (TOL64 if dtype == "f64" else TOL32)
-    if dtype == "f64":
-        assert rel_l2(y2[nodes], ys) <= TOL64
+    assert rel_l2(y2[nodes], ys) <= (TOL64 if dtype == "f64" else TOL32)
 
 
 @pytest.mark.gpu
@@ -239,14 +283,15 @@ def test_largest_case_count_R64(dtype):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 4])
 def test_fully_constrained_mesh_is_identity(variant):
-    """Every DOF fixed: K_bc = I, so every kernel must return x exactly."""
+    """Every DOF fixed: K_bc = I, so every kernel must return x exactly (the
+    paired kernel computes FP32 products only)."""
     ensure_lib()
     from paper_1710_08679_gb300 import fe
     m = MESHES["box2"]()
     M = fe.Mesh(m.coords, m.conn, m.young, m.poisson, np.zeros_like(m.free))
-    for dtype in (torch.float64, torch.float32):
+    for dtype in ((torch.float32,) if variant == 4 else (torch.float64, torch.float32)):
         x = torch.from_numpy(mg.random_vectors(m.n_nodes, 4, seed=9)).to(dtype)
         y = run(M, x.numpy().astype(np.float64), dtype, variant, tile=8)
         assert np.array_equal(y, x.double().numpy())
