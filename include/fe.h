@@ -193,13 +193,22 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *   FE_EBE_GATHER_X2  FP32 products only (R in {4, 8, 16, 32}): the gather
  *                  kernel with each thread computing two cases of one element
  *                  (r and r + R/2) in paired FP32 instructions (two lanes per
- *                  multiply-add), sharing the element's geometry between them. */
+ *                  multiply-add), sharing the element's geometry between them;
+ *   FE_EBE_COLOUR  elements coloured so that no two of one colour share a node
+ *                  (greedy, built on first use); one launch per colour, one
+ *                  thread per (element, case), results added into y with plain
+ *                  loads and stores instead of atomics (the scatter by element
+ *                  colouring of the paper's K-computer design, Sec. 3.2.2).
+ *                  Deterministic: the same inputs give bitwise the same y.
+ *                  fe_ebe_set_variant ignores tile_elems; fe_ebe_get_variant
+ *                  returns the number of colours there. */
 typedef enum {
   FE_EBE_DIRECT = 0,
   FE_EBE_TILED = 1,
   FE_EBE_GATHER = 2,
   FE_EBE_GATHER_DF = 3,
-  FE_EBE_GATHER_X2 = 4
+  FE_EBE_GATHER_X2 = 4,
+  FE_EBE_COLOUR = 5
 } fe_ebe_variant;
 
 /*

@@ -222,6 +222,54 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// element colouring (greedy, first fit, elements in internal order): each element
+// takes the lowest colour that none of the elements sharing one of its nodes has
+// taken, read from a per-node bit set of used colours (up to 256 colours)
+// ---------------------------------------------------------------------------
+void build_colouring(fe_mesh* m, cudaStream_t s) {
+  Colouring& c = m->colouring;
+  if (c.ready) return;
+  constexpr int W = 4;  // 64-bit words of colour bits per node
+  const int64_t E = m->n_elem;
+  std::vector<uint64_t> used((size_t)m->n_nodes * W, 0);
+  std::vector<int32_t> colour((size_t)E);
+  int n_colours = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t* nd = &m->conn_host[(size_t)(10 * e)];
+    int col = -1;
+    for (int w = 0; w < W && col < 0; ++w) {
+      uint64_t taken = 0;
+      for (int a = 0; a < 10; ++a) taken |= used[(size_t)nd[a] * W + w];
+      if (~taken) {
+        uint64_t free_bits = ~taken;
+        int b = 0;
+        while (!(free_bits & 1)) {
+          free_bits >>= 1;
+          ++b;
+        }
+        col = 64 * w + b;
+      }
+    }
+    FE_REQUIRE(col >= 0, "element colouring needs more than %d colours", 64 * W);
+    for (int a = 0; a < 10; ++a) used[(size_t)nd[a] * W + col / 64] |= uint64_t(1) << (col % 64);
+    colour[(size_t)e] = col;
+    n_colours = std::max(n_colours, col + 1);
+  }
+  // group by colour (counting sort keeps internal order within a colour)
+  c.ptr.assign((size_t)n_colours + 1, 0);
+  for (int64_t e = 0; e < E; ++e) c.ptr[(size_t)colour[(size_t)e] + 1]++;
+  for (int k = 0; k < n_colours; ++k) c.ptr[(size_t)k + 1] += c.ptr[(size_t)k];
+  std::vector<int64_t> pos(c.ptr.begin(), c.ptr.end() - 1);
+  std::vector<int32_t> elems((size_t)E);
+  for (int64_t e = 0; e < E; ++e) elems[(size_t)pos[(size_t)colour[(size_t)e]]++] = (int32_t)e;
+  c.elems.alloc(elems.size() * sizeof(int32_t));
+  FE_CUDA(cudaMemcpyAsync(c.elems.ptr, elems.data(), elems.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaStreamSynchronize(s));
+  c.n_colours = n_colours;
+  c.ready = true;
+}
+
+// ---------------------------------------------------------------------------
 // materials upload (internal element order)
 // ---------------------------------------------------------------------------
 static void upload_materials(fe_mesh* m, cudaStream_t s) {
@@ -430,7 +478,7 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
-                   variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2,
+                   variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2 || variant == FE_EBE_COLOUR,
                "unknown variant %d", variant);
     FE_REQUIRE(variant != FE_EBE_GATHER_DF || (dtype == FE_F64 && df_supported(R)),
                "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
@@ -439,6 +487,11 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     DeviceGuard dg(m->device);
     if (variant == FE_EBE_DIRECT) {
       ebe_set_variant(m, R, dtype == FE_F32, 0);
+      return;
+    }
+    if (variant == FE_EBE_COLOUR) {
+      build_colouring(m, (cudaStream_t)stream);
+      ebe_set_variant(m, R, dtype == FE_F32, FE_EBE_COLOUR * 65536 + m->colouring.n_colours);
       return;
     }
     FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),

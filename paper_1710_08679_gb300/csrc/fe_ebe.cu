@@ -112,6 +112,51 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ebe_direct_kern
 }
 
 // ---------------------------------------------------------------------------
+// colour kernel: thread = (element of one colour, case). No two elements of a
+// colour share a node, and the colours run one launch after another on one
+// stream, so each free value of y is read, increased and written by one thread
+// at a time: no atomics, and the summation order is fixed (deterministic y).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ebe_colour_kernel(
+    MeshView<T> M, int R, const int32_t* __restrict__ elems, int64_t n, const uint16_t* __restrict__ own,
+    const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= n * R) return;
+  const int64_t i = gid / R;
+  const int r = (int)(gid - i * R);
+  const int64_t e = __ldg(elems + i);
+  int nd[10];
+  load_conn<T>(M.conn, e, nd);
+  ElemGeo<T> G;
+  load_geometry(M, e, nd, G);
+  T u[10][3];
+  int mk[10];
+#pragma unroll
+  for (int a = 0; a < 10; ++a) {
+    mk[a] = __ldg(M.nmask + nd[a]);
+    const T* xa = x + ((int64_t)nd[a] * R + r) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[a][c] = ((mk[a] >> c) & 1) ? __ldg(xa + c) : T(0);
+  }
+  T yl[10][3];
+  elem_apply(G, u, yl);
+  const int ow = __ldg(own + e);
+#pragma unroll
+  for (int a = 0; a < 10; ++a) {
+    T* ya = y + ((int64_t)nd[a] * R + r) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if ((mk[a] >> c) & 1)
+        ya[c] += yl[a][c];
+      else if ((ow >> a) & 1)   // constrained DOF: (I - P) x, written once by the node's owner element
+        ya[c] = __ldg(x + ((int64_t)nd[a] * R + r) * 3 + c);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // tiled kernel: CTA = tile of elements. Shared memory holds the tile's node
 // inputs and accumulated outputs as [local node][R][3], the element geometry
 // (computed once per element, shared by its R case threads) and the local
@@ -984,6 +1029,21 @@ static void launch_direct(const fe_mesh* m, int R, const T* x, T* y, cudaStream_
   FE_CHECK_LAUNCH();
 }
 
+template <typename T>
+static void launch_colour(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip) {
+  const Colouring& c = m->colouring;
+  FE_REQUIRE(c.ready, "element colouring was not built");
+  const MeshView<T> M = m->view<T>();
+  for (int k = 0; k < c.n_colours; ++k) {
+    const int64_t n = c.ptr[(size_t)k + 1] - c.ptr[(size_t)k];
+    if (n == 0) continue;
+    const int64_t blocks = (n * R + kThreads - 1) / kThreads;
+    ebe_colour_kernel<T><<<(unsigned)blocks, kThreads, 0, s>>>(M, R, c.elems.as<int32_t>() + c.ptr[(size_t)k], n,
+                                                              m->own_elem.as<uint16_t>(), x, y, skip);
+    FE_CHECK_LAUNCH();
+  }
+}
+
 static int max_smem_optin(int device) {
   int v = 0;
   FE_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
@@ -1174,6 +1234,11 @@ template <typename T>
 void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const int* skip) {
   const int v = ebe_get_variant(m, R, sizeof(T) == 4);
   const int kind = v / 65536, tile = v % 65536;
+  if (kind == FE_EBE_COLOUR) {
+    zero_pass<T>(m, R, y, s, skip);
+    launch_colour<T>(m, R, x, y, s, skip);
+    return;
+  }
   if (kind != FE_EBE_DIRECT) {
     auto it = m->tilings.find(tile);
     FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
@@ -1254,7 +1319,8 @@ template void ebe_apply<double>(const fe_mesh*, int, const double*, double*, cud
 // of ones, 2 warm-up and 5 timed products each, CUDA events on `s`) and keeps
 // the fastest. Candidates, where the tile's shared-memory footprint fits: direct;
 // gather with 12..256 elements per tile; tiled with 24..96; for FP64 the
-// float-float gather with 4..24; for FP32 the paired-arithmetic gather with 16..96.
+// float-float gather with 4..24; for FP32 the paired-arithmetic gather with 16..96;
+// and the colour-by-colour kernel.
 template <typename T>
 static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* best_ms) {
   const size_t n = (size_t)m->n_nodes * R * 3;
@@ -1277,12 +1343,16 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   if (sizeof(T) == 4 && x2_supported(R))
     for (int te : {16, 24, 32, 48, 64, 96})
       if (tiled_fits(m, te, R, 1, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_X2 * 65536 + te);
+  cands.push_back(FE_EBE_COLOUR * 65536);  // the colour count is filled in once the colouring exists
   *best_variant = 0;
   *best_ms = 1e30f;
   const int old = m->variant[sizeof(T) == 4][R];
   ensure_geometry_buffer(m, sizeof(T) == 4);
   for (int v : cands) {
-    if (v > 0) {
+    if (v / 65536 == FE_EBE_COLOUR) {
+      build_colouring(m, s);
+      v = FE_EBE_COLOUR * 65536 + m->colouring.n_colours;
+    } else if (v > 0) {
       get_tiling(m, v % 65536, s);
       if (v / 65536 == FE_EBE_GATHER_DF) {
         if (!df_fits(m, v % 65536, R)) continue;

@@ -113,6 +113,15 @@ struct Tiling {
   DevBuf packets;
 };
 
+// Element colouring: no two elements of one colour share a node, so the products
+// of one colour can be added into y without atomics (one launch per colour).
+struct Colouring {
+  bool ready = false;
+  int n_colours = 0;
+  std::vector<int64_t> ptr;  // [n_colours + 1] offsets into elems
+  DevBuf elems;              // int32 [E] internal element ids grouped by colour, ascending within a colour
+};
+
 // Byte layout of a tile packet (host and device agree on it):
 //   int32 {nn, ne, 0, 0} | int32 ids[nnmax] | uint8 mask[nnmax] | uint8 own[nnmax] |
 //   uint16 inc_start[nnmax + 1] | uint16 lconn[te * 10] | uint16 inc[te * 10]
@@ -215,6 +224,8 @@ struct fe_mesh {
   fe::DevBuf geodf;     // float-float geometry [E][16] for the float-float FP64 kernel
   std::vector<int32_t> conn_host;  // [E][10] in internal order
   std::vector<uint8_t> nmask_host; // [N] free-DOF bits
+  // element colouring for the colour-by-colour EBE kernel (built on first use)
+  fe::Colouring colouring;
   // TET4 coarse level (built on first use)
   fe::Coarse coarse;
   // solver workspace (allocated lazily per R)
@@ -244,6 +255,7 @@ bool df_fits(const fe_mesh* m, int tile_elems, int R);
 bool x2_supported(int R);
 bool x2_fits(const fe_mesh* m, int tile_elems, int R);
 const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
+void build_colouring(fe_mesh* m, cudaStream_t s);
 // largest tile (elements) whose shared-memory footprint fits for (R, precision)
 bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);
 
