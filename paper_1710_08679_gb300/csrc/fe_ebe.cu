@@ -759,7 +759,8 @@ __global__ void __launch_bounds__(PipeThreads<T, CPT>::value) ebe_pipe_kernel(in
     // 48: two chunks per thread leave a short second round that the CTA waits for).
     constexpr int QP = (CPT == 2 && CPN % 2 == 0) ? 2 : 1;
     constexpr int CQ = CPN / QP;
-    constexpr int U = 4 / QP;  // incidences per iteration (4 independent loads in flight)
+    constexpr int U = QP >= 4 ? 1 : 4 / QP;  // incidences per iteration (up to 4 loads in flight)
+    static_assert(U >= 1, "the incidence loop must advance");
     for (int k = threadIdx.x; k < nn * CQ; k += blockDim.x) {
       const int ln = k / CQ;
       const int q0 = k - ln * CQ;
