@@ -398,6 +398,61 @@ __global__ void __launch_bounds__(kThreads) spmv4_group_kernel(int64_t N4, int R
   o[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
 }
 
+// the same product from the sliced copy of the matrix: a warp's threads cover whole
+// 8-row slices, so each of the 9 value loads and the column load of a block reads
+// one sector for 8 rows (from the plain [nnzb][9] layout each read 8 sectors: ncu
+// showed the L1 88 % busy and 13 sectors per load request)
+__global__ void __launch_bounds__(kThreads) spmv4_sliced_kernel(int64_t N4, int R, const int32_t* __restrict__ rowptr,
+                                                                const int32_t* __restrict__ sl_off,
+                                                                const int32_t* __restrict__ sl_cols,
+                                                                const float* __restrict__ sl_vals,
+                                                                const float* __restrict__ x, float* __restrict__ y,
+                                                                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int G = R / 4;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= N4 * G) return;
+  const int64_t a = gid / G;
+  const int r0 = (int)(gid - a * G) * 4;
+  const int rr = (int)(a & 7);
+  const int len = __ldg(rowptr + a + 1) - __ldg(rowptr + a);
+  const int64_t base = __ldg(sl_off + (a >> 3));
+  float acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = 0.f;
+  for (int t = 0; t < len; ++t) {
+    const int64_t slot = base + t;
+    const int64_t b = __ldg(sl_cols + slot * 8 + rr);
+    const float* B = sl_vals + slot * 72 + rr;
+    float m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = __ldg(B + 8 * k);
+    const float4* xb = reinterpret_cast<const float4*>(x + (b * R + r0) * 3);
+    const float4 v0 = __ldg(xb), v1 = __ldg(xb + 1), v2 = __ldg(xb + 2);
+    const float v[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        acc[3 * w + i] += m[3 * i] * v[3 * w] + m[3 * i + 1] * v[3 * w + 1] + m[3 * i + 2] * v[3 * w + 2];
+  }
+  float4* o = reinterpret_cast<float4*>(y + (a * R + r0) * 3);
+  o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  o[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+}
+
+// copies the assembled blocks into the sliced layout
+__global__ void slice_values_kernel(int64_t nnzb, const int32_t* __restrict__ pos, const float* __restrict__ vals,
+                                    float* __restrict__ sl_vals) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nnzb) return;
+  const int p = pos[q];
+  float* dst = sl_vals + (int64_t)(p >> 3) * 72 + (p & 7);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dst[8 * k] = vals[9 * q + k];
+}
+
 // diagonal 3x3 blocks of K1: V [(lam + mu) g_a g_a^T + mu |g_a|^2 I] per corner
 __global__ void jacobi4_diag_kernel(MeshView<double> M, const int32_t* __restrict__ conn4, double* __restrict__ Dg) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -613,7 +668,39 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2) {
     c.cols.alloc(cols.size() * 4);
     FE_CUDA(cudaMemcpyAsync(c.rowptr.ptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
     FE_CUDA(cudaMemcpyAsync(c.cols.ptr, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, s));
-    FE_CUDA(cudaStreamSynchronize(s));
+    // sliced layout: slice k holds rows 8k..8k+7 and as many slots as its longest row
+    {
+      const int64_t ns = (N4 + 7) / 8;
+      std::vector<int32_t> off((size_t)ns + 1, 0);
+      for (int64_t k = 0; k < ns; ++k) {
+        int L = 0;
+        for (int64_t v = 8 * k; v < std::min<int64_t>(N4, 8 * k + 8); ++v)
+          L = std::max(L, rowptr[(size_t)v + 1] - rowptr[(size_t)v]);
+        FE_REQUIRE((int64_t)off[(size_t)k] + L < (int64_t)INT32_MAX / 72, "coarse matrix too large to slice");
+        off[(size_t)k + 1] = off[(size_t)k] + L;
+      }
+      c.n_slots = off[(size_t)ns];
+      std::vector<int32_t> scol((size_t)c.n_slots * 8), pos(cols.size());
+      for (int64_t k = 0; k < ns; ++k)
+        for (int rr = 0; rr < 8; ++rr)
+          for (int32_t t = 0; t < off[(size_t)k + 1] - off[(size_t)k]; ++t)
+            scol[((size_t)off[(size_t)k] + t) * 8 + rr] = (int32_t)std::min<int64_t>(N4 - 1, 8 * k + rr);
+      for (int64_t v = 0; v < N4; ++v) {
+        const int64_t k = v / 8, rr = v % 8;
+        for (int32_t q = rowptr[(size_t)v]; q < rowptr[(size_t)v + 1]; ++q) {
+          const int64_t slot = off[(size_t)k] + (q - rowptr[(size_t)v]);
+          scol[(size_t)(slot * 8 + rr)] = cols[(size_t)q];
+          pos[(size_t)q] = (int32_t)(slot * 8 + rr);
+        }
+      }
+      c.sl_off.alloc(off.size() * 4);
+      c.sl_cols.alloc(scol.size() * 4);
+      c.sl_pos.alloc(pos.size() * 4);
+      FE_CUDA(cudaMemcpyAsync(c.sl_off.ptr, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s));
+      FE_CUDA(cudaMemcpyAsync(c.sl_cols.ptr, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, s));
+      FE_CUDA(cudaMemcpyAsync(c.sl_pos.ptr, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice, s));
+      FE_CUDA(cudaStreamSynchronize(s));
+    }
     c.rowptr_host = std::move(rowptr);
     c.cols_host = std::move(cols);
     c.csr_pattern = true;
@@ -623,6 +710,7 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2) {
   size_t free_b = 0, total_b = 0;
   FE_CUDA(cudaMemGetInfo(&free_b, &total_b));
   size_t need = (size_t)c.nnzb * 9 * (c.vals32.ptr ? sizeof(double) : sizeof(float) + sizeof(double));
+  if (!c.sl_vals.ptr) need += (size_t)c.n_slots * 72 * sizeof(float);
   if (level2 && !c.l2_ready) need += level2_bytes(m);
   if (need > free_b / 4) return false;
   DevBuf v64, missing;
@@ -641,6 +729,13 @@ bool build_coarse_matrix(fe_mesh* m, cudaStream_t s, bool level2) {
   FE_CUDA(cudaMemcpyAsync(&hmiss, missing.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
   FE_CUDA(cudaStreamSynchronize(s));
   FE_REQUIRE(hmiss == 0, "coarse matrix assembly: block outside the pattern");
+  if (!c.sl_vals.ptr) {
+    c.sl_vals.alloc((size_t)c.n_slots * 72 * sizeof(float));
+    FE_CUDA(cudaMemsetAsync(c.sl_vals.ptr, 0, c.sl_vals.bytes, s));  // padding slots stay zero
+  }
+  slice_values_kernel<<<blocks_for(c.nnzb), kThreads, 0, s>>>(c.nnzb, c.sl_pos.as<int32_t>(), c.vals32.as<float>(),
+                                                               c.sl_vals.as<float>());
+  FE_CHECK_LAUNCH();
   c.csr_ready = true;
   if (level2 && !c.l2_ready) build_level2(m, v64.as<double>(), s);
   return true;
@@ -659,6 +754,13 @@ void bcsr_spmv(int64_t n, int R, const int32_t* rowptr, const int32_t* cols, con
 void coarse_spmv(const fe_mesh* m, int R, const float* x4, float* y4, cudaStream_t s, const int* skip) {
   const Coarse& c = m->coarse;
   FE_REQUIRE(c.csr_ready, "coarse matrix not assembled");
+  if (R % 4 == 0 && c.sl_vals.ptr) {
+    spmv4_sliced_kernel<<<blocks_for(c.n_nodes * (R / 4)), kThreads, 0, s>>>(
+        c.n_nodes, R, c.rowptr.as<int32_t>(), c.sl_off.as<int32_t>(), c.sl_cols.as<int32_t>(), c.sl_vals.as<float>(),
+        x4, y4, skip);
+    FE_CHECK_LAUNCH();
+    return;
+  }
   bcsr_spmv(c.n_nodes, R, c.rowptr.as<int32_t>(), c.cols.as<int32_t>(), c.vals32.as<float>(), x4, y4, s, skip);
 }
 

@@ -159,6 +159,14 @@ struct Coarse {
   int64_t nnzb = 0;
   DevBuf rowptr, cols;      // int32 [N4 + 1], [nnzb] (columns sorted per row)
   DevBuf vals32;            // float [nnzb][9]
+  // sliced copy of K1_bc for the product: rows in slices of 8, slot t of a slice
+  // holds block t of each of its rows, values interleaved by row ([slot][9][8]) so
+  // that one load instruction of a warp reads a value of 8 rows from one sector
+  int64_t n_slots = 0;
+  DevBuf sl_off;            // int32 [slices + 1] first slot of each slice
+  DevBuf sl_cols;           // int32 [n_slots][8] block column (padding: the row itself)
+  DevBuf sl_pos;            // int32 [nnzb] slot * 8 + row in slice of each block
+  DevBuf sl_vals;           // float [n_slots][9][8]
   std::vector<int32_t> rowptr_host, cols_host, nmask4_host;  // host copies for the level-2 set-up
   // level 2: aggregation of the coarse nodes and its Galerkin matrix A2
   bool l2_pattern = false, l2_ready = false;

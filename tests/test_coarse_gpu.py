@@ -67,8 +67,11 @@ def test_ebe4_matches_assembled_tet4_operator(meshes, name, R, dtype):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("name", ["box8", "crust9x5x4"])
-@pytest.mark.parametrize("R", [1, 3, 16])
+@pytest.mark.parametrize("R", [1, 3, 4, 8, 16, 32])
 def test_assembled_coarse_operator_matches_oracle(meshes, name, R):
+    """R a multiple of 4 takes the sliced copy of the matrix (8 rows per slice; a
+    warp covers 4, 2, 1 or half a slice at R = 4, 8, 16, 32), other R the plain
+    block-CSR arrays."""
     m, cm, M = meshes[name]
     K1 = oracle.assemble4(cm)
     x = mg.random_vectors(cm.vertex.size, R, seed=310 + R).astype(np.float32).astype(np.float64)
@@ -133,6 +136,10 @@ def test_galerkin_identity_at_full_size():
     y_ebe = M.ebe4(x32).double().cpu().numpy()
     y64 = M.ebe4(x32.double()).cpu().numpy()
     assert rel_l2(y_asm, y64) <= TOL32 and rel_l2(y_ebe, y64) <= TOL32
+    # R = 16: the sliced copy of the matrix against the FP64 element-by-element product
+    x16 = (mg.random_vectors(n4, 16, seed=10) * free4[:, None, :]).astype(np.float32)
+    x16t = torch.from_numpy(x16).cuda()
+    assert rel_l2(M.coarse_apply(x16t).double().cpu().numpy(), M.ebe4(x16t.double()).cpu().numpy()) <= TOL32
     # sampled rows against element matrices of the oracle
     rng = np.random.default_rng(3)
     conn4 = np.searchsorted(vertex, m.conn[:, :4])
@@ -261,3 +268,7 @@ def test_set_log_young_rebuilds_coarse_preconditioner(meshes):
     x32 = x.astype(np.float32).astype(np.float64)
     y32 = M.coarse_apply(cuda(x32, torch.float32)).double().cpu().numpy()
     assert rel_l2(y32, oracle.spmv(K1, x32)) <= TOL32
+    # the sliced copy (R a multiple of 4) is refreshed with the new values too
+    x4 = mg.random_vectors(cm.vertex.size, 4, seed=18).astype(np.float32).astype(np.float64)
+    y4 = M.coarse_apply(cuda(x4, torch.float32)).double().cpu().numpy()
+    assert rel_l2(y4, oracle.spmv(K1, x4)) <= TOL32
