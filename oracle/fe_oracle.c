@@ -612,8 +612,9 @@ int oracle_pcg(int64_t N, const int64_t* rowptr, const int32_t* col, const doubl
 }
 
 /* ------------------------------------------------------------------------- */
-/* Flexible (adaptive) CG, Algorithm 1(a) with level 2 dropped, and the FP32   */
-/* inner PCG of Algorithm 1(b), R cases at once                               */
+/* Flexible (adaptive) CG of Algorithm 1(a) with the level-0 inner loop only  */
+/* (levels 1 and 2: oracle_fcg_ml below), and the FP32 inner PCG of          */
+/* Algorithm 1(b), R cases at once                                           */
 /* ------------------------------------------------------------------------- */
 
 /* Algorithm 1(b) on one level, FP32 vectors and products, dots accumulated in FP64:

@@ -1,6 +1,6 @@
 // EBE product y = K_bc x for R cases (Eq. 3, multiple vectors of Sec. 3.1).
 //
-// Two kernels compute the same thing:
+// Several kernels compute the same thing; fe_ebe_tune times them per (R, precision):
 //  * EBE_DIRECT: one thread per (element, case). The thread recomputes the
 //    element geometry, gathers its 30 inputs straight from global memory (the R
 //    threads of one element read the node's 3R contiguous values together) and
@@ -12,8 +12,19 @@
 //    of the tile from shared memory, accumulates them in shared memory and adds
 //    each tile node's total to global memory once. This replaces ~10 global
 //    atomics per element and case with ~(tile nodes / tile elements) of them.
-// Both first write y = (I - P) x (constrained DOFs copy x, free DOFs start at
-// zero) and only ever add into free DOFs, which yields P K P x + (I - P) x.
+//  * EBE_GATHER: tiles as above, but each element-case product goes to its own
+//    shared-memory slot and each tile node sums its slots (no atomics inside the
+//    tile); for 16-byte node rows the persistent pipelined form (prep pass for the
+//    geometry, cp.async prefetch of the next tiles) is used.
+//  * EBE_GATHER_DF: the pipelined gather kernel in float-float arithmetic (FP64
+//    products on the FP32 pipe).
+//  * EBE_GATHER_X2: the pipelined gather kernel with two cases per thread in
+//    paired FP32 instructions.
+//  * EBE_COLOUR: elements coloured so that no two of a colour share a node; one
+//    launch per colour, plain read-modify-write instead of atomics.
+// All write y = (I - P) x on constrained DOFs (copied from x by the node's owner)
+// and only ever add into free DOFs after a zero pass, which yields
+// P K P x + (I - P) x.
 #include <algorithm>
 #include <cstdio>
 
