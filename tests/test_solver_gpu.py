@@ -229,3 +229,40 @@ def test_64_cases_in_one_batch(box8):
     for r in range(64):
         assert stats[r]["relres"] <= 1e-8
         assert rel_l2(u.cpu().numpy()[:, r], ud[:, r]) <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_full_size_two_level_solve_sampled_residual():
+    """The batched solve the benchmark times: 16 unit-slip patches on the 70x70x35
+    crust block (4,234,653 DOF), levels 1 and 0, to true relative residual 1e-8.
+    The right-hand sides come from the oracle (assembled hanging-wall sub-meshes);
+    the residual f - K_bc u is recomputed by the oracle's element-by-element row
+    sums at every node of the patches' elements and at 2,000 random nodes: each
+    entry is bounded by ||f - K_bc u|| <= 1e-8 ||f|| (x2 for the oracle's own
+    rounding). One case is compared with the plain FP64 PCG solve."""
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    m, iface = mg.crust_block()
+    cases = mg.patch_grid_cases(m, iface)[:16]
+    R = len(cases)
+    assert R == 16
+    f = np.zeros((m.n_nodes, R, 3))
+    for r, c in enumerate(cases):
+        sub = mg.Mesh(coords=m.coords, conn=m.conn[c.elems], young=m.young[c.elems], poisson=m.poisson[c.elems],
+                      free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
+        Ks = oracle.assemble(sub, apply_bc=False)
+        f[:, r] = -oracle.spmv(Ks, c.slip[:, None, :])[:, 0] * m.free
+    M = fe.Mesh.from_mesh(m)
+    u, stats, st = M.solve(cuda(f), solver="fcg_mg", tol=1e-8)
+    assert st == 0 and all(s["relres"] <= 1e-8 for s in stats)
+    un = u.cpu().numpy()
+    rng = np.random.default_rng(11)
+    near = np.unique(np.concatenate([m.conn[c.elems].ravel() for c in cases]))
+    nodes = np.unique(np.concatenate([near, rng.integers(0, m.n_nodes, 2000)]))
+    res = f[nodes] - oracle.sampled_product(m, un, nodes)
+    for r in range(R):
+        assert np.abs(res[:, r]).max() <= 2e-8 * np.linalg.norm(f[:, r]), r
+    u1, s1, st1 = M.solve(cuda(f[:, :1]), solver="pcg64", tol=1e-8)
+    assert st1 == 0 and s1[0]["relres"] <= 1e-8
+    assert rel_l2(u1.cpu().numpy()[:, 0], un[:, 0]) <= 1e-4
