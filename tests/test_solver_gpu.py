@@ -266,3 +266,24 @@ def test_full_size_two_level_solve_sampled_residual():
     u1, s1, st1 = M.solve(cuda(f[:, :1]), solver="pcg64", tol=1e-8)
     assert st1 == 0 and s1[0]["relres"] <= 1e-8
     assert rel_l2(u1.cpu().numpy()[:, 0], un[:, 0]) <= 1e-4
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solver", ["fcg_mixed", "fcg_mg"])
+def test_solver_with_paired_and_colour_kernels(solver):
+    """The solvers do not depend on the kernel choice: with the paired-arithmetic
+    kernel for the FP32 products and the colour-by-colour kernel for the FP64 ones
+    (R = 8), the batch reaches 1e-8 and matches the oracle's direct solve."""
+    m = mg.plain_box()
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    R = 8
+    M.set_variant(R, "f32", 4, 24)
+    M.set_variant(R, "f64", 5, 0)
+    assert M.get_variant(R, "f32")[0] == 4 and M.get_variant(R, "f64")[0] == 5
+    f = mg.random_vectors(m.n_nodes, R, seed=41) * m.free[:, None, :]
+    u, stats, st = M.solve(cuda(f), solver=solver, tol=1e-8)
+    assert st == 0 and all(s["relres"] <= 1e-8 for s in stats)
+    ud = oracle.direct_solve(K, f)
+    for r in range(R):
+        assert rel_l2(u.cpu().numpy()[:, r], ud[:, r]) <= 1e-5
