@@ -47,7 +47,10 @@ typedef enum {
   FE_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
   FE_ENOCONV = 4,     /* a solve hit its iteration cap before the tolerance */
   FE_EBREAKDOWN = 5,  /* a solve met a non-positive curvature or a NaN/Inf */
-  FE_ETIMEOUT = 6     /* a bounded device-side wait gave up */
+  FE_ETIMEOUT = 6     /* reserved for a bounded device-side wait that gives up; no kernel of
+                         this version spins on a flag (cp.async groups use hardware waits,
+                         blocks synchronise only through CTA barriers and kernel order),
+                         so no entry point returns it */
 } fe_status;
 
 typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
