@@ -209,7 +209,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
-    m, _ = make_workload(SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x")))
+    shape = SHAPE if not args.shape else tuple(int(v) for v in args.shape.split("x"))
+    m, _ = make_workload(shape)
     import oracle
     sub = oracle_slab(m, 4)
     K = oracle.assemble(sub)
@@ -225,11 +226,13 @@ def run_reference(args):
     out = {"metric": METRIC, "value": val, "unit": "GDOF·cases/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "crust_70x70x35_tet10_slab4", "R": R_MAIN, "mesh_elements": sub.n_elem,
-                      "mesh_dof": 3 * sub.n_nodes},
+           "config": {"workload": "crust_%dx%dx%d_tet10_R%d_fp32_ebe" % (shape + (R_MAIN,)), "R": R_MAIN,
+                      "mesh_elements": m.n_elem, "mesh_dof": 3 * m.n_nodes,
+                      "parallelism": "oracle on the host cores (rate of a bounded sample, per DOF x case)"},
            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": val,
-                            "sample": f"assembled CSR product of the bottom 4 of 35 hexahedron layers "
-                                      f"({sub.n_elem} elements), R = {R_MAIN}, FP64"},
+                            "sample": f"assembled CSR product of the bottom 4 of {shape[2]} hexahedron layers "
+                                      f"({sub.n_elem} elements, {3 * sub.n_nodes} DOF), R = {R_MAIN}, FP64; "
+                                      f"assembly not timed"},
            "e2e": {"value": val, "unit": "GDOF·cases/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
