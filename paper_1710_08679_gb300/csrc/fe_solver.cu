@@ -53,7 +53,8 @@ enum IField { I_ACTIVE = 0, I_CAND, I_RESTART, I_FIRST, I_STATUS, I_OUTER, I_INN
 struct Cases {
   double* d;      // [D_COUNT][R]
   int* i;         // [I_COUNT][R]
-  int* done;      // inner-loop stop flag (1 int), followed by the inner step counter (1 int)
+  int* done;      // inner-loop stop flag (1 int), the inner step counter (1 int), and a flag
+                  // set while every free component of u is zero (1 int; the start skips K u)
   int R;
   __device__ __forceinline__ int& step() const { return done[1]; }
   __device__ __forceinline__ double& D(int f, int r) const { return d[f * R + r]; }
@@ -250,11 +251,13 @@ void build_block_jacobi(fe_mesh* m, cudaStream_t s) {
 // vector kernels (N nodes, R cases; blockDim = K*R)
 // ---------------------------------------------------------------------------
 
-// u <- P u ; fn2 += ||P f||^2
+// u <- P u ; fn2 += ||P f||^2 ; clears the u-is-zero flag (set to 1 before) if a
+// free component of u is nonzero
 __global__ void k_prepare(int64_t N, Cases C, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
                           double* __restrict__ u) {
   extern __shared__ double sm[];
   double acc = 0.0;
+  bool nz = false;
   VEC_LOOP_BEGIN
   const int mk = nmask[n];
   for (int c = 0; c < 3; ++c) {
@@ -262,20 +265,23 @@ __global__ void k_prepare(int64_t N, Cases C, const uint8_t* __restrict__ nmask,
     const double fv = fr ? f[o + c] : 0.0;
     acc += fv * fv;
     if (!fr) u[o + c] = 0.0;
+    else if (u[o + c] != 0.0) nz = true;
   }
   VEC_LOOP_END
+  if (__any_sync(__activemask(), nz) && (threadIdx.x & 31) == 0) atomicAnd(C.done + 2, 0);
   reduce_cases(acc, C.R, blockDim.x / C.R, sm, C.d + D_FN2 * C.R);
 }
 
-// r = P f - q ; rn2 += ||r||^2
+// r = P f - q (q = K u, not computed when u = 0) ; rn2 += ||r||^2
 __global__ void k_residual(int64_t N, Cases C, const uint8_t* __restrict__ nmask, const double* __restrict__ f,
                            const double* __restrict__ q, double* __restrict__ rv) {
   extern __shared__ double sm[];
   double acc = 0.0;
+  const bool u_zero = C.done[2] != 0;
   VEC_LOOP_BEGIN
   const int mk = nmask[n];
   for (int c = 0; c < 3; ++c) {
-    const double v = ((mk >> c) & 1) ? f[o + c] - q[o + c] : 0.0;
+    const double v = ((mk >> c) & 1) ? (u_zero ? f[o + c] : f[o + c] - q[o + c]) : 0.0;
     rv[o + c] = v;
     acc += v * v;
   }
@@ -629,7 +635,10 @@ __global__ void s_init(Cases C) {
   for (int f = 0; f < D_COUNT; ++f) C.D(f, r) = 0.0;
   for (int f = 0; f < I_COUNT; ++f) C.I(f, r) = 0;
   C.I(I_FIRST, r) = 1;
-  if (r == 0) *C.done = 0;
+  if (r == 0) {
+    C.done[0] = 0;
+    C.done[2] = 1;  // u = 0 until k_prepare finds a nonzero free component
+  }
 }
 
 // after ||f||^2 and ||r||^2: cases with f = 0 are finished (u = 0); others start
@@ -1131,10 +1140,10 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
       many->slot_case[(size_t)r] = many->next;
     }
   }
-  // start: u = P u, r = P f - K u, ||f||, ||r||
+  // start: u = P u, r = P f - K u, ||f||, ||r|| (the product is skipped when u = 0)
   S.scal(s_init);
   S.vec(k_prepare, m->nmask.as<uint8_t>(), f, u);
-  ebe_apply<double>(m, R, u, w->q.as<double>(), s);
+  ebe_apply<double>(m, R, u, w->q.as<double>(), s, S.C.done + 2);
   S.vec(k_residual, m->nmask.as<uint8_t>(), f, (const double*)w->q.as<double>(), w->r.as<double>());
   S.scal(s_start, o.tol, 0);
   S.vec(k_zero_trivial, u);
