@@ -269,6 +269,26 @@ def test_full_size_crust_block_sampled_rows(dtype):
 
 
 @pytest.mark.gpu
+@pytest.mark.slow
+def test_full_size_crust_block_R32_paired_kernel():
+    """R = 32 on the full crust block in the configuration the benchmark's sweep
+    reports for it (paired-arithmetic kernel, 24-element tiles): sampled rows
+    against the oracle's element-by-element row sums."""
+    m, _ = mg.crust_block()
+    M = gpu_mesh(m)
+    R = 32
+    x = mg.random_vectors(m.n_nodes, R, seed=100 + R).astype(np.float32).astype(np.float64)
+    y = run(M, x, torch.float32, 4, tile=24)
+    assert M.get_variant(R, "f32") == (4, 24)
+    rng = np.random.default_rng(1)
+    nodes = np.unique(np.concatenate([rng.integers(0, m.n_nodes, 2000), [0, m.n_nodes - 1]]))
+    ys = oracle.sampled_product(m, x, nodes)
+    assert rel_l2(y[nodes], ys) <= TOL32
+    for r in (0, 15, 16, 31):   # both lanes of the pairs (r, r + 16)
+        assert rel_l2(y[nodes, r], ys[:, r]) <= TOL32, r
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_buffer_products_pipeline_across_calls(dtype, pinned):
