@@ -287,3 +287,39 @@ def test_solver_with_paired_and_colour_kernels(solver):
     ud = oracle.direct_solve(K, f)
     for r in range(R):
         assert rel_l2(u.cpu().numpy()[:, r], ud[:, r]) <= 1e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_full_size_many_case_driver_sampled_residual():
+    """The many-case workload at full size (120x120x60 hexahedra, 6 layers,
+    21,083,403 DOF): the first 12 of its 96 unit-slip cases through fe_solve_many
+    with the memory-sized slot count and the two-level solver, right-hand sides
+    from the oracle (assembled hanging-wall sub-meshes). Every case reaches 1e-8;
+    for three cases the oracle recomputes f - K_bc u at every node of the patch's
+    elements and at 1,000 random nodes (each entry bounded by 1e-8 ||f||, x2 for
+    the oracle's rounding)."""
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    m, iface = mg.crust_block(shape=(120, 120, 60), h=1000.0, jitter=0.10, seed=3, n_layers=6)
+    cases = mg.many_cases(m, iface, n_patches=48, seed=3)[:12]
+    F = np.zeros((len(cases), m.n_nodes, 3))
+    for c, sc in enumerate(cases):
+        if len(sc.elems) == 0:
+            continue
+        sub = mg.Mesh(coords=m.coords, conn=m.conn[sc.elems], young=m.young[sc.elems], poisson=m.poisson[sc.elems],
+                      free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
+        F[c] = -oracle.spmv(oracle.assemble(sub, apply_bc=False), sc.slip[:, None, :])[:, 0] * m.free
+    M = fe.Mesh.from_mesh(m)
+    u, stats, st, R_used = M.solve_many(cuda(F), R_slots=0, solver="fcg_mg", tol=1e-8)
+    assert st == 0 and R_used >= 1
+    assert all(s["relres"] <= 1e-8 for s in stats)
+    rng = np.random.default_rng(12)
+    for c in (0, 5, 11):
+        if not F[c].any():
+            continue
+        near = np.unique(m.conn[cases[c].elems].ravel())
+        nodes = np.unique(np.concatenate([near, rng.integers(0, m.n_nodes, 1000)]))
+        uc = u[c].cpu().numpy()[:, None, :]
+        res = F[c][nodes] - oracle.sampled_product(m, uc, nodes)[:, 0]
+        assert np.abs(res).max() <= 2e-8 * np.linalg.norm(F[c]), c
