@@ -74,3 +74,33 @@ def test_two_layer_bspline_slips_solve(problem, solver):
         _, outer, _, _, _ = oracle.fcg_mg(K, F, coarse=cm, free=m.free, tol=1e-8)
         for r in range(F.shape[1]):
             assert abs(stats[r]["outer"] - int(outer[r])) <= max(2, 0.25 * outer[r])
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_full_size_two_layer_model_sampled_residual():
+    """The two-layer workload of the benchmark at full size (70x70x35 hexahedra,
+    4,234,653 DOF, soft 5 km top layer): 16 B-spline dip-slip patches, right-hand
+    sides from the oracle, two-level solve to 1e-8; the oracle recomputes f - K_bc u
+    at every node of the patches' elements and at 2,000 random nodes (each entry
+    bounded by 1e-8 ||f||, x2 for the oracle's rounding)."""
+    ensure_lib()
+    from paper_1710_08679_gb300 import fe
+    m, iface = mg.two_layer_block(shape=(70, 70, 35))
+    cases = mg.patch_grid_cases(m, iface, profile="bspline")[:16]
+    R = len(cases)
+    F = np.zeros((m.n_nodes, R, 3))
+    for r, c in enumerate(cases):
+        sub = mg.Mesh(coords=m.coords, conn=m.conn[c.elems], young=m.young[c.elems], poisson=m.poisson[c.elems],
+                      free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
+        F[:, r] = -oracle.spmv(oracle.assemble(sub, apply_bc=False), c.slip[:, None, :])[:, 0] * m.free
+    M = fe.Mesh.from_mesh(m)
+    u, stats, st = M.solve(cuda(F), solver="fcg_mg", tol=1e-8)
+    assert st == 0 and all(s["relres"] <= 1e-8 for s in stats)
+    un = u.cpu().numpy()
+    rng = np.random.default_rng(13)
+    near = np.unique(np.concatenate([m.conn[c.elems].ravel() for c in cases]))
+    nodes = np.unique(np.concatenate([near, rng.integers(0, m.n_nodes, 2000)]))
+    res = F[nodes] - oracle.sampled_product(m, un, nodes)
+    for r in range(R):
+        assert np.abs(res[:, r]).max() <= 2e-8 * np.linalg.norm(F[:, r]), r
