@@ -233,9 +233,11 @@ def test_64_cases_in_one_batch(box8):
 
 @pytest.mark.gpu
 @pytest.mark.slow
-def test_full_size_two_level_solve_sampled_residual():
-    """The batched solve the benchmark times: 16 unit-slip patches on the 70x70x35
-    crust block (4,234,653 DOF), levels 1 and 0, to true relative residual 1e-8.
+@pytest.mark.parametrize("solver", ["fcg_mg", "fcg_amg"])
+def test_full_size_two_level_solve_sampled_residual(solver):
+    """The batched solves the benchmark times: 16 unit-slip patches on the 70x70x35
+    crust block (4,234,653 DOF), levels 1 and 0 (and levels 2, 1 and 0), to true
+    relative residual 1e-8.
     The right-hand sides come from the oracle (assembled hanging-wall sub-meshes);
     the residual f - K_bc u is recomputed by the oracle's element-by-element row
     sums at every node of the patches' elements and at 2,000 random nodes: each
@@ -254,7 +256,7 @@ def test_full_size_two_level_solve_sampled_residual():
         Ks = oracle.assemble(sub, apply_bc=False)
         f[:, r] = -oracle.spmv(Ks, c.slip[:, None, :])[:, 0] * m.free
     M = fe.Mesh.from_mesh(m)
-    u, stats, st = M.solve(cuda(f), solver="fcg_mg", tol=1e-8)
+    u, stats, st = M.solve(cuda(f), solver=solver, tol=1e-8)
     assert st == 0 and all(s["relres"] <= 1e-8 for s in stats)
     un = u.cpu().numpy()
     rng = np.random.default_rng(11)
