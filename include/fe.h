@@ -47,10 +47,11 @@ typedef enum {
   FE_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
   FE_ENOCONV = 4,     /* a solve hit its iteration cap before the tolerance */
   FE_EBREAKDOWN = 5,  /* a solve met a non-positive curvature or a NaN/Inf */
-  FE_ETIMEOUT = 6     /* reserved for a bounded device-side wait that gives up; no kernel of
-                         this version spins on a flag (cp.async groups use hardware waits,
-                         blocks synchronise only through CTA barriers and kernel order),
-                         so no entry point returns it */
+  FE_ETIMEOUT = 6     /* a bounded device-side wait gave up (reported by fe_mesh_device_status):
+                         the warp-specialised EBE kernel hands tiles between its warps on
+                         mbarriers, each wait limited to about one second of SM clock; a wait
+                         that runs out records it on the mesh and the kernel finishes without
+                         waiting again, so its results are not to be used */
 } fe_status;
 
 typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
@@ -130,6 +131,16 @@ fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, 
 /* Releases every device resource of the mesh (synchronises the device). NULL is a no-op. */
 void fe_mesh_destroy(fe_mesh* mesh);
 
+/*
+ * fe_mesh_device_status -- synchronises `stream`, then reads and clears the mesh's
+ * device status word. Returns FE_ETIMEOUT if a kernel launched on this mesh since
+ * the last call gave up a bounded wait (its products are then invalid), FE_OK
+ * otherwise. fe_ebe_apply does not read it on its own (that would synchronise
+ * every call); fe_pcg_solve and fe_solve_many read it when they finish and then
+ * return FE_ETIMEOUT.
+ */
+fe_status fe_mesh_device_status(const fe_mesh* mesh, void* stream);
+
 /* Node and element counts of a mesh. */
 fe_status fe_mesh_info(const fe_mesh* mesh, int64_t* n_nodes, int64_t* n_elem);
 
@@ -204,14 +215,24 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *                  colouring of the paper's K-computer design, Sec. 3.2.2).
  *                  Deterministic: the same inputs give bitwise the same y.
  *                  fe_ebe_set_variant ignores tile_elems; fe_ebe_get_variant
- *                  returns the number of colours there. */
+ *                  returns the number of colours there;
+ *   FE_EBE_WS      FP32 products only (R in {4, 8, 16, 32}; tile_elems * R / 2 a
+ *                  multiple of 32, at most 384): warp-specialised kernel, one
+ *                  block per SM. Compute warps evaluate two cases of an element per
+ *                  thread in paired FP32 instructions; staging warps load the
+ *                  following tiles' node values and coordinates, compute the
+ *                  element geometry and sum each tile node's element slots into y
+ *                  (one 16-byte atomic add per 4 values). Tiles are grown greedily
+ *                  (each takes the element sharing most nodes with it), built per
+ *                  (tile_elems, R) on first use. */
 typedef enum {
   FE_EBE_DIRECT = 0,
   FE_EBE_TILED = 1,
   FE_EBE_GATHER = 2,
   FE_EBE_GATHER_DF = 3,
   FE_EBE_GATHER_X2 = 4,
-  FE_EBE_COLOUR = 5
+  FE_EBE_COLOUR = 5,
+  FE_EBE_WS = 6
 } fe_ebe_variant;
 
 /*

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfe.so")
-SOURCES = ["fe_api.cu", "fe_ebe.cu", "fe_solver.cu", "fe_adjoint.cu", "fe_coarse.cu", "fe_level2.cu", "fe_host.cu"]
+SOURCES = ["fe_api.cu", "fe_ebe.cu", "fe_ebe_ws.cu", "fe_solver.cu", "fe_adjoint.cu", "fe_coarse.cu", "fe_level2.cu", "fe_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -283,8 +283,14 @@ static void upload_materials(fe_mesh* m, cudaStream_t s) {
     m32[2 * e] = (float)m64[2 * e];
     m32[2 * e + 1] = (float)m64[2 * e + 1];
   }
+  std::vector<float> mv((size_t)E * 4, 0.f);
+  for (int64_t e = 0; e < E; ++e) {
+    mv[(size_t)(4 * e)] = m32[(size_t)(2 * e)];
+    mv[(size_t)(4 * e + 1)] = m32[(size_t)(2 * e + 1)];
+  }
   FE_CUDA(cudaMemcpyAsync(m->mat64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(m->mat32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice, s));
+  FE_CUDA(cudaMemcpyAsync(m->matv.ptr, mv.data(), mv.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaStreamSynchronize(s));
   m->jacobi_ready = false;
   m->coarse.jacobi_ready = false;
@@ -392,6 +398,7 @@ fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, 
     for (int64_t e = 0; e < n_elem; ++e)
       std::memcpy(&m->conn_host[(size_t)e * 10], conn + 10 * m->perm_host[(size_t)e], 10 * sizeof(int32_t));
     m->young_host.assign(young, young + n_elem);
+    m->xyz_host.assign(coords, coords + 3 * n_nodes);
     m->poisson_host.assign(poisson, poisson + n_elem);
     std::vector<float> xyz32((size_t)n_nodes * 3);
     for (int64_t i = 0; i < 3 * n_nodes; ++i) xyz32[(size_t)i] = (float)coords[i];
@@ -403,6 +410,9 @@ fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, 
     m->xyz32.alloc((size_t)n_nodes * 3 * sizeof(float));
     m->mat64.alloc((size_t)n_elem * 2 * sizeof(double));
     m->mat32.alloc((size_t)n_elem * 2 * sizeof(float));
+    m->matv.alloc((size_t)n_elem * 4 * sizeof(float));
+    m->dev_status.alloc(sizeof(int32_t));
+    FE_CUDA(cudaMemsetAsync(m->dev_status.ptr, 0, sizeof(int32_t), s));
     m->nmask.alloc((size_t)n_nodes);
     m->perm.alloc((size_t)n_elem * sizeof(int64_t));
     m->own_elem.alloc((size_t)n_elem * sizeof(uint16_t));
@@ -447,6 +457,24 @@ void fe_mesh_destroy(fe_mesh* m) {
   }
 }
 
+fe_status fe_mesh_device_status(const fe_mesh* m, void* stream) {
+  int32_t v = 0;
+  const fe_status st = guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    FE_CUDA(cudaMemcpyAsync(&v, m->dev_status.ptr, sizeof(v), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemsetAsync(m->dev_status.ptr, 0, sizeof(v), s));
+    FE_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != FE_OK) return st;
+  if (v != 0) {
+    set_error("a device-side wait of the EBE kernel gave up; the products since the last check are invalid");
+    return FE_ETIMEOUT;
+  }
+  return FE_OK;
+}
+
 fe_status fe_mesh_info(const fe_mesh* m, int64_t* n_nodes, int64_t* n_elem) {
   return guarded([&] {
     FE_REQUIRE(m != nullptr, "mesh is NULL");
@@ -478,8 +506,11 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(m != nullptr, "mesh is NULL");
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
-                   variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2 || variant == FE_EBE_COLOUR,
+                   variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2 || variant == FE_EBE_COLOUR ||
+                   variant == FE_EBE_WS,
                "unknown variant %d", variant);
+    FE_REQUIRE(variant != FE_EBE_WS || (dtype == FE_F32 && ws_supported(R)),
+               "the warp-specialised kernel computes FP32 products for R in {4, 8, 16, 32}");
     FE_REQUIRE(variant != FE_EBE_GATHER_DF || (dtype == FE_F64 && df_supported(R)),
                "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
     FE_REQUIRE(variant != FE_EBE_GATHER_X2 || (dtype == FE_F32 && x2_supported(R)),
@@ -492,6 +523,13 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     if (variant == FE_EBE_COLOUR) {
       build_colouring(m, (cudaStream_t)stream);
       ebe_set_variant(m, R, dtype == FE_F32, FE_EBE_COLOUR * 65536 + m->colouring.n_colours);
+      return;
+    }
+    if (variant == FE_EBE_WS) {
+      FE_REQUIRE(tile_elems >= 1 && tile_elems <= 4096, "tile size %d out of range", tile_elems);
+      FE_REQUIRE(ws_fits(m, tile_elems, R), "warp-specialised tiles of %d elements do not fit for R = %d",
+                 tile_elems, R);
+      ebe_set_variant(m, R, 1, FE_EBE_WS * 65536 + tile_elems);
       return;
     }
     FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),

@@ -22,6 +22,8 @@
 //    paired FP32 instructions.
 //  * EBE_COLOUR: elements coloured so that no two of a colour share a node; one
 //    launch per colour, plain read-modify-write instead of atomics.
+//  * EBE_WS (fe_ebe_ws.cu): warp-specialised FP32 kernel, compute warps in paired
+//    arithmetic and staging warps (loads, geometry, node sums) on greedy tiles.
 // All write y = (I - P) x on constrained DOFs (copied from x by the node's owner)
 // and only ever add into free DOFs after a zero pass, which yields
 // P K P x + (I - P) x.
@@ -1251,6 +1253,18 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
     launch_colour<T>(m, R, x, y, s, skip);
     return;
   }
+  if (kind == FE_EBE_WS) {
+    if constexpr (sizeof(T) == 4) {
+      auto it = m->ws_tilings.find(tile * 256 + R);
+      FE_REQUIRE(it != m->ws_tilings.end(), "warp-specialised tiling of %d elements for R = %d was not built", tile,
+                 R);
+      zero_pass<T>(m, R, y, s, skip);
+      launch_ws(m, *it->second, x, y, s, skip);
+    } else {
+      FE_REQUIRE(false, "the warp-specialised kernel computes FP32 products only");
+    }
+    return;
+  }
   if (kind != FE_EBE_DIRECT) {
     auto it = m->tilings.find(tile);
     FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
@@ -1331,7 +1345,8 @@ template void ebe_apply<double>(const fe_mesh*, int, const double*, double*, cud
 // of ones, 2 warm-up and 5 timed products each, CUDA events on `s`) and keeps
 // the fastest. Candidates, where the tile's shared-memory footprint fits: direct;
 // gather with 12..256 elements per tile; tiled with 24..96; for FP64 the
-// float-float gather with 4..24; for FP32 the paired-arithmetic gather with 16..96;
+// float-float gather with 4..24; for FP32 the paired-arithmetic gather with 16..96
+// and the warp-specialised kernel with 256 to 512 element-case items per tile;
 // and the colour-by-colour kernel.
 template <typename T>
 static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* best_ms) {
@@ -1355,6 +1370,9 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   if (sizeof(T) == 4 && x2_supported(R))
     for (int te : {16, 24, 32, 48, 64, 96})
       if (tiled_fits(m, te, R, 1, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_X2 * 65536 + te);
+  if (sizeof(T) == 4 && ws_supported(R))
+    for (int items : {256, 320, 384, 448, 512})   // element-case items per tile: 4 to 8 compute warps
+      if (items % R == 0) cands.push_back(FE_EBE_WS * 65536 + items / R);
   cands.push_back(FE_EBE_COLOUR * 65536);  // the colour count is filled in once the colouring exists
   *best_variant = 0;
   *best_ms = 1e30f;
@@ -1365,8 +1383,10 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
       build_colouring(m, s);
       v = FE_EBE_COLOUR * 65536 + m->colouring.n_colours;
     } else if (v > 0) {
-      get_tiling(m, v % 65536, s);
-      if (v / 65536 == FE_EBE_GATHER_DF) {
+      if (v / 65536 != FE_EBE_WS) get_tiling(m, v % 65536, s);
+      if (v / 65536 == FE_EBE_WS) {
+        if (!ws_fits(m, v % 65536, R)) continue;
+      } else if (v / 65536 == FE_EBE_GATHER_DF) {
         if (!df_fits(m, v % 65536, R)) continue;
       } else if (v / 65536 == FE_EBE_GATHER_X2) {
         if (!x2_fits(m, v % 65536, R)) continue;

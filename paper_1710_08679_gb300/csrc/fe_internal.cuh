@@ -196,6 +196,21 @@ struct HostPipe {
   ~HostPipe();
 };
 
+// Tiles of the warp-specialised EBE kernel (fe_ebe_ws.cu), built per (tile size, R):
+// elements grouped by greedy growth (each tile adds the element sharing most nodes
+// with it), one packet per tile with the tile's node ids, element ids, slot offsets
+// and row offsets for R cases (see WsLayout in fe_ebe_ws.cu).
+struct WsTiling {
+  int te = 0;             // elements per tile (the last tiles may hold fewer)
+  int R = 0;              // cases the offsets are laid out for
+  int nnmax = 0;          // largest node count of a tile
+  int nvmax = 0;          // largest virtual-node count of a tile (node-sum tasks per 4 cases)
+  int pk_bytes = 0;       // bytes per packet (multiple of 16)
+  int64_t n_tiles = 0;
+  double nodes_per_elem = 0.0;  // sum of tile node counts / elements
+  DevBuf packets;
+};
+
 struct SolverWork;  // defined in fe_solver.cu
 
 }  // namespace fe
@@ -218,6 +233,12 @@ struct fe_mesh {
   fe::DevBuf binv32;    // float [N][9]
   // element tilings for the shared-memory EBE kernel, by elements per tile (built lazily)
   std::map<int, std::unique_ptr<fe::Tiling>> tilings;
+  // tilings of the warp-specialised kernel, by tile size * 256 + R (built lazily)
+  std::map<int, std::unique_ptr<fe::WsTiling>> ws_tilings;
+  fe::DevBuf xyz4;      // float4 [N]: FP32 coordinates padded to 16 bytes (built with the first WS tiling)
+  fe::DevBuf matv;      // float4 [E]: (E, nu, 0, 0) in FP32, 16-byte rows for bulk copies
+  fe::DevBuf dev_status;  // int32: set by a kernel whose bounded wait gave up (fe_mesh_device_status)
+  std::vector<double> xyz_host;  // [N][3] coordinates as given
   // EBE kernel per precision (0 = FP64, 1 = FP32) and R: -1 = default, else
   // kind * 65536 + elements per tile (kind: fe_ebe_variant)
   int32_t variant[2][65];
@@ -266,6 +287,12 @@ const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);
 void build_colouring(fe_mesh* m, cudaStream_t s);
 // largest tile (elements) whose shared-memory footprint fits for (R, precision)
 bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);
+
+// Warp-specialised FP32 kernel (fe_ebe_ws.cu), R in {4, 8, 16, 32}
+bool ws_supported(int R);
+const WsTiling* get_ws_tiling(fe_mesh* m, int tile_elems, int R, cudaStream_t s);
+bool ws_fits(fe_mesh* m, int tile_elems, int R);
+void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip);
 
 // Block Jacobi (fe_solver.cu)
 void build_block_jacobi(fe_mesh* m, cudaStream_t s);

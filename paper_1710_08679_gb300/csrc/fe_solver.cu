@@ -1275,7 +1275,14 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
     }
     FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
+    int32_t dev_status = 0;   // a bounded device-side wait of an EBE kernel gave up during the solve
+    FE_CUDA(cudaMemcpyAsync(&dev_status, m->dev_status.ptr, sizeof(dev_status), cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
+    if (dev_status != 0) {
+      FE_CUDA(cudaMemsetAsync(m->dev_status.ptr, 0, sizeof(int32_t), s));
+      set_error("fe_pcg_solve: a device-side wait of the EBE kernel gave up; the solution is invalid");
+      throw Failure{FE_ETIMEOUT};
+    }
     for (int c = 0; c < R && !many; ++c) {
       int st = hi[I_STATUS * R + c];
       double rel = hd[D_RELRES * R + c];

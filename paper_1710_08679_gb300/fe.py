@@ -34,7 +34,7 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
             "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
             "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info",
-            "fe_ebe_apply_host"]
+            "fe_ebe_apply_host", "fe_mesh_device_status"]
 
 
 class FeError(RuntimeError):
@@ -103,12 +103,13 @@ def load(path: Optional[str] = None):
     lib.fe_level2_block_jacobi.argtypes = [_vp, _vp, _vp]
     lib.fe_coarse_matrix_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]
     lib.fe_ebe_apply_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
+    lib.fe_mesh_device_status.argtypes = [_vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
                  "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
                  "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
-                 "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host"):
+                 "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host", "fe_mesh_device_status"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -252,6 +253,11 @@ class Mesh:
         _check(load().fe_ebe_tune(self._h, int(R), dt, self._stream(), ctypes.byref(v), ctypes.byref(t)),
                "fe_ebe_tune")
         return v.value, t.value
+
+    def device_status(self):
+        """Synchronise the current stream and raise FeError(FE_ETIMEOUT) if a kernel on
+        this mesh gave up a bounded device-side wait since the last check."""
+        _check(load().fe_mesh_device_status(self._h, self._stream()), "fe_mesh_device_status")
 
     def set_log_young(self, logE):
         torch = _torch()
