@@ -51,9 +51,11 @@ def parse():
                     help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
-    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer", "coarse", "solve", "adjoint"],
+    ap.add_argument("--workload", default="ebe", choices=["ebe", "many", "two_layer", "coarse", "solve", "adjoint", "cpu_solves"],
                     help="ebe: the EBE line on the 70x70x35 crust block (default); many: 96 unit-slip cases on "
-                         "the 120x120x60 block through fe_solve_many vs the plain FP64 PCG one case at a time")
+                         "the 120x120x60 block through fe_solve_many vs the plain FP64 PCG one case at a time; "
+                         "cpu_solves: the oracle's plain PCG timed on the host cores on the solve meshes")
+    ap.add_argument("--cpu-solves-small", action="store_true", help="cpu_solves on 24x24x12 meshes (testing only)")
     ap.add_argument("--many-cases", type=int, default=96, help="cases of --workload many")
     ap.add_argument("--many-plain", type=int, default=1, help="cases timed with the plain FP64 PCG")
     ap.add_argument("--solver", choices=["pcg64", "fcg_mixed", "fcg_mg", "fcg_amg"], default="fcg_mg",
@@ -79,6 +81,32 @@ def aggregate(units_per_rank: float, elapsed_ms: float, dist=None, device=None):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     tmax = float(t.item())
     return units_per_rank * world / (tmax * 1e-3), tmax
+
+
+def shard_cases(n_cases: int, world: int, rank: int) -> range:
+    """The contiguous block of case indices rank `rank` of `world` solves: sizes differ
+    by at most one, earlier ranks take the larger blocks, every case goes to exactly
+    one rank. Cases are independent right-hand sides, so the ranks exchange nothing
+    while they solve."""
+    if world < 1 or not 0 <= rank < world or n_cases < 0:
+        raise ValueError("bad shard request")
+    q, r = divmod(n_cases, world)
+    start = rank * q + min(rank, r)
+    return range(start, start + q + (1 if rank < r else 0))
+
+
+def aggregate_sharded(units_this_rank: float, elapsed_ms: float, dist=None, device=None):
+    """Whole-job throughput when ranks did different numbers of units: (sum of the
+    units over ranks / slowest rank's time, max elapsed ms, total units). Two
+    all-reduces after the timed region, none inside it."""
+    import torch
+    u = torch.tensor([float(units_this_rank)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    if dist is not None and dist.get_world_size() > 1:
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total, tmax = float(u.item()), float(t.item())
+    return total / (tmax * 1e-3), tmax, total
 
 
 def dist_env():
@@ -402,6 +430,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu and world == 1:
         try:
             out["cpu_baseline"] = cpu_baseline(m, R)
+            out["cpu_baseline"]["solve"] = cpu_solve_baseline(torch, fe)
         except Exception as exc:  # report, never fail the line
             out["cpu_baseline"] = {"error": str(exc)[:200]}
     if rank == 0:
@@ -411,122 +440,272 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def timed_solve(M, f, torch, reps=3, **kw):
+    """One untimed solve (workspace, block Jacobi, coarse levels and kernel choices
+    are set up on first use and then kept), then `reps` timed solves of the same
+    batch; wall time to all cases converged (including the per-call graph capture)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, stats, st = M.solve(f, raise_on_fail=False, **kw)
+    torch.cuda.synchronize()
+    first = time.perf_counter() - t0
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, stats, st = M.solve(f, raise_on_fail=False, **kw)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    return u, stats, st, {"first_call_seconds": first, "seconds_median": float(np.median(times)),
+                          "seconds_min": float(np.min(times)), "seconds_max": float(np.max(times)), "repeats": reps}
+
+
+def lanczos_condition(coef):
+    """Extreme eigenvalues of M^-1 K from the CG coefficients of one case (the Lanczos
+    tridiagonal: T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_k,k+1 = sqrt(beta_k)/alpha_k)."""
+    from scipy.linalg import eigh_tridiagonal
+    al, be = coef[:, 0], coef[:, 1]
+    k = int(np.count_nonzero(al))
+    al, be = al[:k], be[:k]
+    d = 1.0 / al
+    d[1:] += be[:-1] / al[:-1]
+    e = np.sqrt(be[:-1]) / al[:-1]
+    ev = eigh_tridiagonal(d, e, eigvals_only=True)
+    return float(ev[0]), float(ev[-1]), k
+
+
+def block_condition(M, free):
+    """Condition number of the block-Jacobi matrix M (the 3x3 diagonal blocks of K
+    over each node's free components), from the inverse blocks the library builds."""
+    B = M.block_jacobi().cpu().numpy()
+    lo, hi = np.inf, 0.0
+    for pat in np.unique(free, axis=0):
+        idx = np.flatnonzero(pat)
+        if idx.size == 0:
+            continue
+        sel = np.all(free == pat, axis=1)
+        ev = 1.0 / np.linalg.eigvalsh(B[sel][:, idx][:, :, idx])
+        lo, hi = min(lo, float(ev.min())), max(hi, float(ev.max()))
+    return hi / lo
+
+
 def run_solves(m, iface, M, torch, fe, world, profile="uniform",
                workload="crust_70x70x35_tet10 16 unit-slip patches (4x4 grid, 2x2 km)"):
     """Batched mixed FCG (R = 16 unit-slip patches) vs plain FP64 PCG, one case
-    at a time, on the same mesh; both to true relative residual 1e-8."""
+    at a time, on the same mesh; both to true relative residual 1e-8. Every solver:
+    one untimed solve, then three timed ones (median, min, max). The displacement
+    error is bounded by kappa_est * relres, kappa_est = kappa(M) kappa(M^-1 K) with
+    kappa(M^-1 K) from the Lanczos tridiagonal of the plain PCG's coefficients."""
     R = 16
     f = slip_rhs(m, iface, R, M, torch, fe, profile)
     M.tune(R, "f64")
     M.tune(1, "f64")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    u, stats, st = M.solve(f, solver="fcg_mixed", tol=1e-8, raise_on_fail=False)
-    torch.cuda.synchronize()
-    t_mixed = time.perf_counter() - t0
-    ok = all(s["relres"] <= 1e-8 for s in stats)
-    # plain FP64 PCG, one case at a time (two cases timed, per-case time averaged)
-    n_plain = 2
-    t_plain = []
-    plain_stats = []
-    for r in range(n_plain):
-        fr = f[:, r:r + 1, :].contiguous()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ur, sr, _ = M.solve(fr, solver="pcg64", tol=1e-8, raise_on_fail=False)
-        torch.cuda.synchronize()
-        t_plain.append(time.perf_counter() - t0)
-        plain_stats.append(sr[0])
-        du = torch.linalg.norm(ur[:, 0] - u[:, r]) / torch.linalg.norm(ur[:, 0])
-        plain_stats[-1]["rel_diff_vs_mixed"] = float(du)
-    mixed_rate = R / t_mixed
-    plain_rate = 1.0 / float(np.mean(t_plain))
-    # the same batch with the TET4 level (inner loop level 1) before level 0; the
-    # coarse mesh, its block Jacobi and its assembled operator are per-mesh set-up,
-    # built before the timed solve and reported separately
+    M.tune(R, "f32")
+    out = {"workload": workload, "timing": "one untimed solve, then the median of 3 timed solves (min/max given)"}
+    # set-up of the coarse levels, once per mesh (reported, not in the solve times)
     t0 = time.perf_counter()
     M.coarse_block_jacobi()
     n4 = M.coarse_info()[0]
     M.coarse_apply(torch.zeros((n4, R, 3), dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
-    t_coarse_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    u2, stats2, st2 = M.solve(f, solver="fcg_mg", tol=1e-8, raise_on_fail=False)
-    torch.cuda.synchronize()
-    t_mg = time.perf_counter() - t0
-    du2 = float(torch.linalg.norm(u2 - u) / torch.linalg.norm(u))
-    mg_rate = R / t_mg
-    # and with the aggregation level (inner loop level 2) as well: Algorithm 1 in full
+    coarse_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     M.level2_info()
     torch.cuda.synchronize()
-    t_l2_setup = time.perf_counter() - t0
-    torch.cuda.synchronize()
+    l2_setup = time.perf_counter() - t0
+    # plain FP64 PCG, one case at a time (three cases), recording the CG coefficients of the first
+    coef = np.zeros((4000, 1, 2))
+    plain = []
+    for r in range(3):
+        fr = f[:, r:r + 1, :].contiguous()
+        ur, sr, _, tm = timed_solve(M, fr, torch, reps=1, solver="pcg64", tol=1e-8,
+                                    **({"cg_coef": coef} if r == 0 else {}))
+        plain.append((ur, sr[0], tm))
+    lmin, lmax, kc = lanczos_condition(coef[:, 0, :])
+    kappa_pk = lmax / lmin
+    kappa_m = block_condition(M, m.free)
+    kappa = kappa_pk * kappa_m
+    plain_s = [p[2]["seconds_median"] for p in plain]
+    plain_rate = 1.0 / float(np.mean(plain_s))
+    out["plain_pcg64_one_case"] = {
+        "case_solves_per_s": plain_rate * world, "seconds_per_case": plain_s,
+        "first_call_seconds": plain[0][2]["first_call_seconds"], "iters": [p[1]["outer"] for p in plain],
+        "relres": [p[1]["relres"] for p in plain]}
+    out["condition_estimate"] = {"kappa_MinvK_lanczos": kappa_pk, "lanczos_steps": kc, "lambda_min": lmin,
+                                 "lambda_max": lmax, "kappa_M_blocks": kappa_m, "kappa_est": kappa,
+                                 "note": "||u - u*|| / ||u*|| <= kappa_est * relres (kappa(K) <= kappa(M) kappa(M^-1 K))"}
+    runs = [("mixed_fcg", dict(solver="fcg_mixed")),
+            ("mixed_fcg_two_level", dict(solver="fcg_mg")),
+            ("mixed_fcg_three_level", dict(solver="fcg_amg")),
+            ("mixed_fcg_two_level_gb300_loops", dict(solver="fcg_mg", **GB300_LOOPS))]
+    u_ref = None
+    for name, kw in runs:
+        u, stats, st, tm = timed_solve(M, f, torch, reps=3, tol=1e-8, **kw)
+        relmax = max(s["relres"] for s in stats)
+        entry = {"case_solves_per_s": R / tm["seconds_median"] * world, **tm,
+                 "case_solves_per_s_min_max": [R / tm["seconds_max"] * world, R / tm["seconds_min"] * world],
+                 "all_converged": all(s["relres"] <= 1e-8 for s in stats), "status": int(st),
+                 "outer": [s["outer"] for s in stats], "inner0": [s["inner"] for s in stats],
+                 "inner1": [s["inner1"] for s in stats], "inner2": [s["inner2"] for s in stats],
+                 "relres_max": relmax, "displacement_error_bound": kappa * relmax,
+                 "speedup_vs_plain": (R / tm["seconds_median"]) / plain_rate}
+        if kw.get("n_inner") is not None or name.endswith("gb300_loops"):
+            entry["loops"] = GB300_LOOPS
+        if u_ref is None:
+            u_ref = u
+        else:
+            entry["rel_diff_vs_one_level"] = float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref))
+        # the plain solves of the first three cases against this batch
+        entry["rel_diff_vs_plain"] = [float(torch.linalg.norm(p[0][:, 0] - u[:, r]) / torch.linalg.norm(p[0][:, 0]))
+                                      for r, p in enumerate(plain)]
+        out[name] = entry
+    out["mixed_fcg_two_level"]["coarse_setup_seconds"] = coarse_setup
+    out["mixed_fcg_three_level"]["level2_setup_seconds"] = l2_setup
+    for name, _ in runs:
+        out["speedup" + name[len("mixed_fcg"):]] = out[name]["speedup_vs_plain"]
+    return out
+
+
+def cpu_solve_baseline(torch, fe):
+    """Solve leg of the CPU baseline on the plain box (8^3 hexahedra, 3,072 TET10,
+    14,739 DOF, one double couple): the oracle's block-Jacobi PCG to 1e-8 timed
+    with one thread and with every host core (assembly timed apart), and, as the
+    displacement error of the GPU solvers, their solutions against the oracle's
+    sparse direct solution of the same system."""
+    import oracle
+    from paper_1710_08679_gb300 import meshgen as mg
+    m = mg.plain_box()
+    f = mg.plain_box_rhs(m)
+    cores = os.cpu_count()
     t0 = time.perf_counter()
-    u3, stats3, st3 = M.solve(f, solver="fcg_amg", tol=1e-8, raise_on_fail=False)
-    torch.cuda.synchronize()
-    t_amg = time.perf_counter() - t0
-    du3 = float(torch.linalg.norm(u3 - u) / torch.linalg.norm(u))
-    amg_rate = R / t_amg
-    # the paper tuned its inner-loop settings (its table: 0.1/30, 0.05/300) for
-    # its machines; on GB300 an outer iteration's FP64 product is dear relative to
-    # FP32 inner work, and tighter inner loops (fewer outer iterations) pay
-    loops = GB300_LOOPS
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    u4, stats4, st4 = M.solve(f, solver="fcg_mg", tol=1e-8, raise_on_fail=False, **loops)
-    torch.cuda.synchronize()
-    t_tuned = time.perf_counter() - t0
-    du4 = float(torch.linalg.norm(u4 - u) / torch.linalg.norm(u))
-    tuned_rate = R / t_tuned
-    return {"workload": workload,
-            "mixed_fcg": {"case_solves_per_s": mixed_rate * world, "seconds": t_mixed, "all_converged": ok,
-                          "outer": [s["outer"] for s in stats], "inner": [s["inner"] for s in stats],
-                          "relres_max": max(s["relres"] for s in stats), "status": int(st)},
-            "mixed_fcg_two_level": {"case_solves_per_s": mg_rate * world, "seconds": t_mg,
-                                    "all_converged": all(s["relres"] <= 1e-8 for s in stats2),
-                                    "outer": [s["outer"] for s in stats2], "inner0": [s["inner"] for s in stats2],
-                                    "inner1": [s["inner1"] for s in stats2],
-                                    "relres_max": max(s["relres"] for s in stats2), "status": int(st2),
-                                    "rel_diff_vs_one_level": du2, "coarse_setup_seconds": t_coarse_setup},
-            "mixed_fcg_three_level": {"case_solves_per_s": amg_rate * world, "seconds": t_amg,
-                                      "all_converged": all(s["relres"] <= 1e-8 for s in stats3),
-                                      "outer": [s["outer"] for s in stats3], "inner0": [s["inner"] for s in stats3],
-                                      "inner1": [s["inner1"] for s in stats3],
-                                      "inner2": [s["inner2"] for s in stats3],
-                                      "relres_max": max(s["relres"] for s in stats3), "status": int(st3),
-                                      "rel_diff_vs_one_level": du3, "level2_setup_seconds": t_l2_setup},
-            "plain_pcg64_one_case": {"case_solves_per_s": plain_rate * world, "seconds_per_case": float(np.mean(t_plain)),
-                                     "iters": [s["outer"] for s in plain_stats],
-                                     "relres": [s["relres"] for s in plain_stats],
-                                     "rel_diff_vs_mixed": [s["rel_diff_vs_mixed"] for s in plain_stats]},
-            "mixed_fcg_two_level_gb300_loops": {"case_solves_per_s": tuned_rate * world, "seconds": t_tuned,
-                                                "loops": loops,
-                                                "all_converged": all(s["relres"] <= 1e-8 for s in stats4),
-                                                "outer": [s["outer"] for s in stats4],
-                                                "inner0": [s["inner"] for s in stats4],
-                                                "inner1": [s["inner1"] for s in stats4],
-                                                "relres_max": max(s["relres"] for s in stats4), "status": int(st4),
-                                                "rel_diff_vs_one_level": du4},
-            "speedup": mixed_rate / plain_rate, "speedup_two_level": mg_rate / plain_rate,
-            "speedup_three_level": amg_rate / plain_rate, "speedup_two_level_gb300_loops": tuned_rate / plain_rate}
+    K = oracle.assemble(m)
+    t_asm = time.perf_counter() - t0
+    out = {"kind": "oracle", "unit": "case-solves/s", "assembly_seconds": t_asm,
+           "sample": "plain box 8^3 hexahedra (3,072 TET10, 14,739 DOF), one double couple, FP64 block-Jacobi "
+                     "PCG to 1e-8; assembly not in the rate"}
+    for n in (1, cores):
+        oracle.set_num_threads(n)
+        t0 = time.perf_counter()
+        u_cg, it, rel = oracle.pcg(K, f, tol=1e-8)
+        dt = time.perf_counter() - t0
+        out["threads_%d" % n] = {"cores": oracle.num_threads(), "seconds": dt, "case_solves_per_s": 1.0 / dt,
+                                 "iters": int(it[0]), "relres": float(rel[0])}
+    oracle.set_num_threads(cores)
+    out["value"], out["cores"] = out["threads_%d" % cores]["case_solves_per_s"], cores
+    ud = oracle.direct_solve(K, f)
+    out["oracle_pcg_error_vs_direct"] = float(np.linalg.norm(u_cg - ud) / np.linalg.norm(ud))
+    M = fe.Mesh.from_mesh(m)
+    gpu = {}
+    for name in ("pcg64", "fcg_mixed", "fcg_mg"):
+        u, stats, st = M.solve(torch.from_numpy(f).cuda(), solver=name, tol=1e-8, raise_on_fail=False)
+        gpu[name] = {"relres": stats[0]["relres"], "outer": stats[0]["outer"],
+                     "displacement_error_vs_oracle_direct": float(np.linalg.norm(u.cpu().numpy() - ud) /
+                                                                  np.linalg.norm(ud))}
+    M.close()
+    out["gpu_displacement_error"] = gpu
+    return out
+
+
+def run_cpu_solves(args):
+    """The oracle's plain FP64 PCG on the bench meshes, timed on the host cores: the
+    plain box solved in full (cpu_solve_baseline), the 70x70x35 crust block with its
+    first two slip cases and the 120x120x60 block with its first case. On the two
+    large meshes the oracle runs a bounded number of iterations and the full solve
+    is projected from its seconds per iteration times the iteration count the GPU's
+    plain FP64 PCG needs for the same right-hand side (measured here); assembly
+    and block-Jacobi set-up are timed apart."""
+    import torch
+    import oracle
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08679_gb300 import fe
+    from paper_1710_08679_gb300 import meshgen as mg
+    cores = os.cpu_count()
+    out = {"metric": "oracle case-solves/s (plain FP64 block-Jacobi PCG to 1e-8) on the host cores",
+           "impl": "oracle", "host_cores": cores, "plain_box": cpu_solve_baseline(torch, fe)}
+    for key, shape, n_cases, maker, iters in (
+            ("crust_70x70x35_2_cases", (70, 70, 35), 2, "patch", (20, 5)),
+            ("crust_120x120x60_1_case", (120, 120, 60), 1, "many", (6, 2))):
+        if args.cpu_solves_small:
+            shape = (24, 24, 12)
+        if maker == "patch":
+            m, iface = make_workload(shape)
+            M = fe.Mesh.from_mesh(m)
+            f = slip_rhs(m, iface, n_cases, M, torch, fe)
+        else:
+            m, iface = mg.crust_block(shape=shape, h=1000.0, jitter=0.10, seed=3, n_layers=6)
+            M = fe.Mesh.from_mesh(m)
+            sc = mg.many_cases(m, iface, n_patches=1, seed=3)[0]
+            sub = mg.Mesh(coords=m.coords, conn=m.conn[sc.elems], young=m.young[sc.elems],
+                          poisson=m.poisson[sc.elems], free=np.ones_like(m.free), shape=m.shape, h=m.h,
+                          lengths=m.lengths)
+            Ms = fe.Mesh.from_mesh(sub)
+            free = torch.from_numpy(m.free.astype(np.float64)).cuda()
+            f = (-Ms.ebe(torch.from_numpy(np.ascontiguousarray(sc.slip[:, None, :])).cuda()) *
+                 free[:, None, :]).contiguous()
+            Ms.close()
+        gpu_iters = []
+        for r in range(n_cases):
+            _, st_r, _ = M.solve(f[:, r:r + 1, :].contiguous(), solver="pcg64", tol=1e-8, raise_on_fail=False)
+            gpu_iters.append(int(st_r[0]["outer"]))
+        M.close()
+        fh = f.cpu().numpy()
+        del f
+        torch.cuda.empty_cache()
+        oracle.set_num_threads(cores)
+        t0 = time.perf_counter()
+        K = oracle.assemble(m)
+        t_asm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Minv = oracle.block_jacobi(K)
+        t_bj = time.perf_counter() - t0
+        entry = {"mesh_elements": m.n_elem, "mesh_dof": 3 * m.n_nodes, "cases": n_cases,
+                 "assembly_seconds": t_asm, "block_jacobi_seconds": t_bj, "gpu_pcg64_iters": gpu_iters}
+        for n, k in ((cores, iters[0]), (1, iters[1])):
+            oracle.set_num_threads(n)
+            t0 = time.perf_counter()
+            oracle.pcg(K, fh, tol=1e-30, maxit=k, Minv=Minv)
+            per_it = (time.perf_counter() - t0) / k
+            proj = per_it * max(gpu_iters)       # the batch runs until its slowest case converges
+            entry["threads_%d" % n] = {"cores": oracle.num_threads(), "iterations_timed": k,
+                                       "seconds_per_iteration": per_it, "projected_solve_seconds": proj,
+                                       "projected_case_solves_per_s": n_cases / proj}
+        oracle.set_num_threads(cores)
+        out[key] = entry
+        del K, Minv, fh
+    out["value"] = out["crust_70x70x35_2_cases"]["threads_%d" % cores]["projected_case_solves_per_s"]
+    out["unit"] = "case-solves/s"
+    print(json.dumps(out), flush=True)
 
 
 def run_many(args):
     """96 unit-slip cases (48 patches x strike/dip) on the 120x120x60-hexahedra,
     6-layer crust block (5,184,000 TET10, 21,083,403 DOF) through fe_solve_many
     (memory-aware slot count, converged slots refilled) against the plain FP64
-    PCG one case at a time; both to true relative residual 1e-8."""
+    PCG one case at a time; both to true relative residual 1e-8. Under torchrun
+    the cases are sharded over the ranks (shard_cases): every rank builds the
+    mesh, solves its own block of cases with no exchange, and the job's time is
+    the slowest rank's (strong scaling: the 96 cases are fixed)."""
     import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
     import __graft_entry__
-    __graft_entry__.build()
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
     from paper_1710_08679_gb300 import fe
     from paper_1710_08679_gb300 import meshgen as mg
     shape = (120, 120, 60) if not args.shape else tuple(int(v) for v in args.shape.split("x"))
     t0 = time.perf_counter()
     m, iface = mg.crust_block(shape=shape, h=1000.0, jitter=0.10, seed=3, n_layers=6)
-    M = fe.Mesh.from_mesh(m)
-    cases = mg.many_cases(m, iface, n_patches=(args.many_cases + 1) // 2, seed=3)[:args.many_cases]
+    M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
+    cases_all = mg.many_cases(m, iface, n_patches=(args.many_cases + 1) // 2, seed=3)[:args.many_cases]
+    mine = shard_cases(len(cases_all), world, rank)
+    cases = [cases_all[c] for c in mine]
     F = torch.zeros((len(cases), m.n_nodes, 3), dtype=torch.float64, device="cuda")
     free = torch.from_numpy(m.free.astype(np.float64)).cuda()
     for c, sc in enumerate(cases):
@@ -534,7 +713,7 @@ def run_many(args):
             continue
         sub = mg.Mesh(coords=m.coords, conn=m.conn[sc.elems], young=m.young[sc.elems], poisson=m.poisson[sc.elems],
                       free=np.ones_like(m.free), shape=m.shape, h=m.h, lengths=m.lengths)
-        Ms = fe.Mesh.from_mesh(sub)
+        Ms = fe.Mesh.from_mesh(sub, device=torch.cuda.current_device())
         F[c] = -Ms.ebe(torch.from_numpy(np.ascontiguousarray(sc.slip[:, None, :])).cuda())[:, 0, :] * free
         Ms.close()
     # kernels for the slot count the memory-aware admission picks (32 here) are tuned
@@ -545,37 +724,59 @@ def run_many(args):
         M.coarse_block_jacobi()
         M.coarse_matrix_info()          # assembled coarse matrices (and level 2) before the timed call
     setup_s = time.perf_counter() - t0
+    loops = GB300_LOOPS if args.many_loops == "gb300" else {}
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loops = GB300_LOOPS if args.many_loops == "gb300" else {}
     u, stats, st, R_used = M.solve_many(F, R_slots=0, solver=args.many_solver, tol=1e-8, raise_on_fail=False,
                                         **loops)
     torch.cuda.synchronize()
     t_many = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    rate, tmax_ms, total = aggregate_sharded(len(cases), 1e3 * t_many, dist if world > 1 else None, "cuda")
+    if world > 1:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, {"stats": stats, "status": int(st), "slots": R_used, "seconds": t_many})
+        stats = [s for g in gathered for s in g["stats"]]
+        st = max(g["status"] for g in gathered)
+        per_rank = [{"cases": len(g["stats"]), "seconds": g["seconds"], "slots": g["slots"]} for g in gathered]
+    else:
+        per_rank = [{"cases": len(cases), "seconds": t_many, "slots": R_used}]
     plain = []
-    for c in range(min(args.many_plain, len(cases))):
-        fr = F[c].reshape(m.n_nodes, 1, 3).contiguous()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        ur, sr, _ = M.solve(fr, solver="pcg64", tol=1e-8, raise_on_fail=False)
-        torch.cuda.synchronize()
-        plain.append({"seconds": time.perf_counter() - t1, "iters": sr[0]["outer"], "relres": sr[0]["relres"],
-                      "rel_diff_vs_many": float(torch.linalg.norm(ur[:, 0] - u[c]) / torch.linalg.norm(ur[:, 0]))})
-    rate = len(cases) / t_many
+    if rank == 0:
+        for c in range(min(args.many_plain, len(cases))):
+            fr = F[c].reshape(m.n_nodes, 1, 3).contiguous()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ur, sr, _ = M.solve(fr, solver="pcg64", tol=1e-8, raise_on_fail=False)
+            torch.cuda.synchronize()
+            plain.append({"seconds": time.perf_counter() - t1, "iters": sr[0]["outer"], "relres": sr[0]["relres"],
+                          "rel_diff_vs_many": float(torch.linalg.norm(ur[:, 0] - u[c]) / torch.linalg.norm(ur[:, 0]))})
     plain_rate = 1.0 / float(np.mean([p["seconds"] for p in plain])) if plain else None
-    out = {"metric": "case-solves/s at 1e-8 residual, many-case admission vs plain FP64", "value": rate,
-           "unit": "case-solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
-           "config": {"workload": "crust_%dx%dx%d_tet10_%d_slip_cases" % (shape + (len(cases),)),
-                      "mesh_elements": m.n_elem, "mesh_dof": 3 * m.n_nodes, "slots": R_used,
-                      "solver": args.many_solver, "inner_loops": args.many_loops, "setup_seconds": setup_s},
-           "many": {"seconds": t_many, "status": int(st), "all_converged": all(s["relres"] <= 1e-8 for s in stats),
-                    "outer_min_max": [min(s["outer"] for s in stats), max(s["outer"] for s in stats)],
-                    "inner0_total": sum(s["inner"] for s in stats), "inner1_total": sum(s["inner1"] for s in stats),
-                    "inner2_total": sum(s["inner2"] for s in stats),
-                    "relres_max": max(s["relres"] for s in stats)},
-           "plain_pcg64_one_case": {"case_solves_per_s": plain_rate, "cases": plain},
-           "speedup": rate / plain_rate if plain_rate else None}
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        out = {"metric": "case-solves/s at 1e-8 residual, many-case admission vs plain FP64", "value": rate,
+               "unit": "case-solves/s", "n_gpus": world, "higher_is_better": True,
+               "scaling": "strong", "dtype": "f64+f32", "data": "synthetic",
+               "config": {"workload": "crust_%dx%dx%d_tet10_%d_slip_cases" % (shape + (int(total),)),
+                          "mesh_elements": m.n_elem, "mesh_dof": 3 * m.n_nodes, "slots": R_used,
+                          "solver": args.many_solver, "inner_loops": args.many_loops, "setup_seconds": setup_s,
+                          "parallelism": "cases sharded over %d rank(s), no exchange while solving" % world},
+               "many": {"seconds": tmax_ms * 1e-3, "per_rank": per_rank, "status": int(st),
+                        "all_converged": all(s["relres"] <= 1e-8 for s in stats),
+                        "outer_min_max": [min(s["outer"] for s in stats), max(s["outer"] for s in stats)],
+                        "inner0_total": sum(s["inner"] for s in stats), "inner1_total": sum(s["inner1"] for s in stats),
+                        "inner2_total": sum(s["inner2"] for s in stats),
+                        "relres_max": max(s["relres"] for s in stats)},
+               "plain_pcg64_one_case": {"case_solves_per_s": plain_rate, "cases": plain,
+                                        "note": "rank 0, one GPU"},
+               "speedup": rate / plain_rate / world if plain_rate else None,
+               "speedup_note": "job rate / (plain one-case rate x n_gpus): per-GPU speed-up over the plain solve"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_two_layer(args):
@@ -625,12 +826,12 @@ def run_adjoint(args):
     M = fe.Mesh.from_mesh(m)
     sources = torch.from_numpy(mg.adjoint_sources(m)).cuda()
     obs_np = mg.surface_observations(m, 1000, (500.0, 7500.0), 2)
-    obs = adjoint.Observation(obs_np.node, obs_np.weight)
+    obs = adjoint.Observation(M, obs_np.node, obs_np.weight)
     opts = dict(solver="fcg_mg", tol=1e-8)
     a = torch.ones(16, dtype=torch.float64, device="cuda")
     M.set_log_young(torch.from_numpy(mg.adjoint_true_logE(m)).cuda())
     G, _, _ = M.solve(sources, **opts)
-    clean = obs.apply(torch.einsum("nkc,k->nc", G, a))
+    clean = obs.apply(M.combine_cases(G, a))
     rms = torch.sqrt(torch.mean(clean ** 2))
     d = clean + 0.05 * rms * torch.from_numpy(mg.noise(tuple(clean.shape), 2)).cuda()
     logE0 = torch.from_numpy(np.log(m.young)).cuda()
@@ -764,6 +965,8 @@ def main():
         run_one_solve(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "cpu_solves":
+        run_cpu_solves(args)
     else:
         run_ours(args)
 

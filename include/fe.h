@@ -49,9 +49,11 @@ typedef enum {
   FE_EBREAKDOWN = 5,  /* a solve met a non-positive curvature or a NaN/Inf */
   FE_ETIMEOUT = 6     /* a bounded device-side wait gave up (reported by fe_mesh_device_status):
                          the warp-specialised EBE kernel hands tiles between its warps on
-                         mbarriers, each wait limited to about one second of SM clock; a wait
-                         that runs out records it on the mesh and the kernel finishes without
-                         waiting again, so its results are not to be used */
+                         mbarriers, and the persistent inner-loop kernel of the solvers
+                         meets at grid-wide barriers; each wait is limited to about one
+                         second of SM clock, and a wait that runs out records it on the mesh
+                         and the kernel finishes without waiting again, so its results are
+                         not to be used */
 } fe_status;
 
 typedef enum { FE_F64 = 0, FE_F32 = 1 } fe_dtype;
@@ -85,6 +87,15 @@ typedef struct {
                             2 element by element */
   int32_t n_inner2;      /* FCG_AMG: cap on level-2 inner steps per outer iteration (3000) */
   double eps_inner2;     /* FCG_AMG: level-2 inner stop, the same rule as eps_inner (0.025) */
+  double* cg_coef;       /* PCG64 only, optional (NULL: not recorded): host double
+                            [cg_coef_len][R][2] receiving (alpha_k, beta_k) of CG iteration k
+                            of every case (0 after the case stopped); the coefficients give
+                            the Lanczos tridiagonal of M^-1 K, hence condition estimates */
+  int32_t cg_coef_len;   /* iterations cg_coef holds */
+  int32_t inner_kernel;  /* inner loops on the assembled levels 1 and 2 (R = 4, 8, 16 or 32):
+                            0 one persistent cooperative kernel per loop (default; its CTAs
+                            meet at grid-wide barriers with bounded waits, see FE_ETIMEOUT);
+                            1 one launch per vector pass and scalar step */
 } fe_solve_opts;
 
 /* Per-case results of fe_pcg_solve. */
@@ -107,7 +118,7 @@ const char* fe_version(void);
 /* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
  * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1, n_inner1 300,
  * eps_inner1 0.05, n_inner2 3000, eps_inner2 0.025 (the paper's table of loop settings,
- * levels 0, 1 and 2), coarse_op 0. */
+ * levels 0, 1 and 2), coarse_op 0, cg_coef NULL, cg_coef_len 0, inner_kernel 0. */
 void fe_solve_opts_default(fe_solve_opts* opts);
 
 /*
@@ -310,19 +321,23 @@ fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void* stream);
 /*
  * fe_block_jacobi_noalloc -- fe_block_jacobi's result without allocating device
  * memory. The paper has no counterpart; this exists for callers that cannot
- * allocate where they need the preconditioner: code recording a CUDA stream
- * capture, latency-critical loops that must not take the allocator's lock, and
- * processes whose device memory is held by another allocator's pool.
+ * allocate where they need the preconditioner: latency-critical loops that must
+ * not take the allocator's lock, and processes whose device memory is held by
+ * another allocator's pool (a framework's caching allocator), where a fresh
+ * cudaMalloc can fail mid-run.
  *   binv_dev  device double [N][3][3], overwritten with the inverse blocks
  * Scratch lives in a fixed file-scope device array (about 13.5 MiB, held on every
  * GPU that loads the library until the process exits), so the mesh may have at
  * most 131,072 nodes; larger meshes get FE_EINVAL and nothing is launched.
  * Recomputes the blocks on every call (the mesh's own copy is not touched).
- * Synchronous on `stream` (it reads back an error flag). The first call on a
- * device looks up the array's device address (set-up, once per device); make that
- * first call before any stream capture. All calls share the one array: calls
- * whose work overlaps on the GPU (different streams or threads) race and must be
- * serialised by the caller.
+ * The call synchronises `stream`: it copies an error flag back to the host and
+ * returns only when the blocks are written. The first call on a device looks up
+ * the array's device address (set-up, once per device) and keeps it for the life
+ * of the process; make that first call before any stream capture. The kept address
+ * does not survive a reset of the device's primary context (cudaDeviceReset): do
+ * not call this after one. All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams or threads) race and must be serialised
+ * by the caller.
  */
 fe_status fe_block_jacobi_noalloc(const fe_mesh* mesh, double* binv_dev, void* stream);
 
@@ -338,6 +353,44 @@ fe_status fe_block_jacobi_noalloc(const fe_mesh* mesh, double* binv_dev, void* s
  */
 fe_status fe_adjoint_grad(const fe_mesh* mesh, int32_t R, const double* u_dev, const double* lambda_dev,
                           double* g_elem_dev, void* stream);
+
+/*
+ * Vector steps of the misfit gradient around fe_adjoint_grad (no counterpart in
+ * the paper; the paper's Sec. 5 computes the Green's functions u_k of unit slips,
+ * this completes a least-squares inversion workflow over them). All arrays FP64.
+ *
+ * fe_obs_create -- observation operator u_obs[p] = sum_j w[p][j] u[node[p][j]]
+ * (for instance quadratic interpolation on the surface triangle holding each
+ * observation point).
+ *   n_obs, n_per   observations and nodes per observation (1..64)
+ *   node, weight   host int32 / double [n_obs][n_per], node ids of the mesh (checked
+ *                  on the host; FE_EINVAL names the first bad entry)
+ * The operator lives on the mesh's device; release it with fe_obs_destroy.
+ */
+typedef struct fe_obs fe_obs;     /* opaque, library-owned */
+fe_status fe_obs_create(const fe_mesh* mesh, int64_t n_obs, int32_t n_per, const int32_t* node,
+                        const double* weight, fe_obs** out);
+void fe_obs_destroy(fe_obs* obs);
+
+/* u_obs_dev [n_obs][R][3] = Obs u_dev [N][R][3] (each value summed in a fixed order). */
+fe_status fe_obs_apply(const fe_obs* obs, int32_t R, const double* u_dev, double* u_obs_dev, void* stream);
+
+/* out_dev [N][R][3] = P Obs^T g_dev, g_dev [n_obs][R][3]: the adjoint right-hand side
+ * of a misfit of the observations; constrained DOFs are zero. Overwrites out_dev;
+ * sums in atomic order (reproducible to rounding). */
+fe_status fe_obs_adjoint(const fe_mesh* mesh, const fe_obs* obs, int32_t R, const double* g_dev, double* out_dev,
+                         void* stream);
+
+/* u_dev [N][3] = sum_r a_dev[r] G_dev[:, r, :] for G_dev [N][R][3] (the displacement
+ * of source amplitudes a from the Green's functions of R sources). */
+fe_status fe_combine_cases(const fe_mesh* mesh, int32_t R, const double* G_dev, const double* a_dev, double* u_dev,
+                           void* stream);
+
+/* out_dev[r] = (P f_r) . lam for f_dev [N][R][3], lam_dev [N][3]: dJ/da_r for sources
+ * f_r whose amplitudes a_r scale them, with lam the adjoint state. Overwrites out_dev
+ * [R]; block partial sums added atomically (reproducible to rounding). */
+fe_status fe_case_dots(const fe_mesh* mesh, int32_t R, const double* f_dev, const double* lam_dev, double* out_dev,
+                       void* stream);
 
 /*
  * TET4 coarse level (Sec. 2 and Algorithm 1(a): inner loop level 1).

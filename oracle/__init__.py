@@ -73,6 +73,8 @@ def configure(lib):
         lib.oracle_adjoint_grad.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p, _u8p,
                                             ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = None
         lib.oracle_pattern_n.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _i32p, _i64p, _i32p]
         lib.oracle_pattern_n.restype = ctypes.c_int64
         lib.oracle_tet4_stiffness.argtypes = [_f64p, ctypes.c_double, ctypes.c_double, _f64p]
@@ -109,6 +111,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (timing of the CPU baseline)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def element_stiffness(xe: np.ndarray, E: float, nu: float) -> np.ndarray:

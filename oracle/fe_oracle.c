@@ -44,6 +44,15 @@
 /* VTK TET10 edges: local node 4+q lies at the midpoint of corners EDGE[q][0..1] */
 static const int EDGE[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
 
+/* thread count of the OpenMP loops (timing of the CPU baseline on one core or all) */
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -334,6 +334,9 @@ void fe_solve_opts_default(fe_solve_opts* o) {
   o->coarse_op = 0;
   o->n_inner2 = 3000;
   o->eps_inner2 = 0.025;
+  o->cg_coef = nullptr;
+  o->cg_coef_len = 0;
+  o->inner_kernel = 0;
 }
 
 fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,

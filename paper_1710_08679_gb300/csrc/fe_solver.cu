@@ -56,6 +56,8 @@ struct Cases {
   int* done;      // inner-loop stop flag (1 int), the inner step counter (1 int), and a flag
                   // set while every free component of u is zero (1 int; the start skips K u)
   int R;
+  double* hist = nullptr;   // PCG64: (alpha, beta) per iteration and case, [hist_len][R][2] (optional)
+  int hist_len = 0;
   __device__ __forceinline__ int& step() const { return done[1]; }
   __device__ __forceinline__ double& D(int f, int r) const { return d[f * R + r]; }
   __device__ __forceinline__ int& I(int f, int r) const { return i[f * R + r]; }
@@ -71,6 +73,7 @@ struct SolverWork {
   DevBuf tu, tq;                  // double [N][3] (single-case true residual)
   DevBuf tall;                    // double [N][R][3] (true residuals of several cases at once, lazily)
   DevBuf d, i;                    // case state
+  DevBuf pers;                    // persistent inner loop: sums [2][3][R], barrier and abort words
   cudaStream_t stream = nullptr;
   cudaStream_t body = nullptr;    // records the bodies of the graph's inner-loop nodes
   cudaEvent_t ev = nullptr;
@@ -696,6 +699,11 @@ __global__ void s_pcg_beta(Cases C, double tol, int max_it) {
   const double rn = C.D(D_RHOA, r);
   C.D(D_BETA, r) = rn / C.D(D_RHO, r);
   C.D(D_RHO, r) = rn;
+  const int k = C.I(I_OUTER, r);
+  if (C.hist && k < C.hist_len) {
+    C.hist[((int64_t)k * C.R + r) * 2] = C.D(D_ALPHA, r);
+    C.hist[((int64_t)k * C.R + r) * 2 + 1] = C.D(D_BETA, r);
+  }
   C.I(I_OUTER, r) += 1;
   const double rn2 = C.D(D_RN2, r), fn2 = C.D(D_FN2, r);
   if (!isfinite(rn2)) {
@@ -839,6 +847,332 @@ __global__ void s_outer_check(Cases C, double tol, int max_outer) {
 }
 
 // ---------------------------------------------------------------------------
+// One inner loop (Algorithm 1(b)) on an assembled block-CSR level (levels 1
+// and 2) as a single persistent kernel. The per-step launches above cost more
+// than the arithmetic on these levels (a few MB per vector), so here all steps
+// run in one cooperative launch whose CTAs meet at grid-wide barriers: three
+// per step (after the new search direction, after q = A p and its dot, after
+// the update and its two dots). Every CTA evaluates the per-case scalars
+// (alpha, beta, the stop rule) itself from the reduced sums, so they agree
+// without a further exchange; CTA 0 records them and the step counts in the
+// case state. The arithmetic of each vector pass is that of k_inner_resid,
+// k_inner_p, k_dot and k_inner_update. A thread owns 4 cases of a node (R a
+// power of two from 4 to 32), so its cases are the same in every pass.
+// Each barrier wait is bounded (about a second of SM clock); a wait that runs
+// out sets the mesh's status word, raises the kernel's abort flag (which the
+// other CTAs see in their waits) and every CTA returns.
+// ---------------------------------------------------------------------------
+struct InnerArgs {
+  int64_t N;
+  Cases C;
+  const float* B;                                  // [N][9] inverse diagonal blocks
+  const float* rb;
+  float *ub, *eb, *pb, *qb;                        // [N][R][3]
+  const int32_t* rowptr;                           // [N + 1]
+  const int32_t* cols;                             // plain block CSR [nnzb]
+  const float* vals;                               // [nnzb][9]
+  const int32_t* sl_off;                           // sliced copy (optional): [slices + 1]
+  const int32_t* sl_cols;                          // [slots][8]
+  const float* sl_vals;                            // [slots][9][8]
+  int n_inner;
+  double eps;
+  int f_rbn2, f_count;
+  double* acc;                                     // [2][3][R] per-parity sums: gamma, ||e||^2, rho
+  unsigned* bar;                                   // [2] arrival count, generation
+  int* abort_flag;
+  int* status;
+  long long timeout;
+};
+
+enum { A_GAM = 0, A_EN2 = 1, A_RHO = 2 };
+
+__device__ __forceinline__ double* acc_at(const InnerArgs& A, int parity, int field) {
+  return A.acc + ((size_t)parity * 3 + field) * A.C.R;
+}
+
+// grid-wide barrier of a cooperative launch; false once any CTA gave up a wait
+__device__ __forceinline__ bool grid_barrier(const InnerArgs& A) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = A.bar + 1;
+    volatile int* abort_flag = A.abort_flag;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(A.bar, 1u) == gridDim.x - 1) {
+      atomicExch(A.bar, 0u);
+      __threadfence();
+      atomicAdd(A.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0 && !*abort_flag) {
+        if (clock64() - t0 > A.timeout) {
+          atomicExch(A.abort_flag, 1);
+          atomicExch(A.status, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = !*abort_flag;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// q (12 values: 4 cases x 3) of block row a times x, cases r0 .. r0 + 3
+template <bool SLICED>
+__device__ __forceinline__ void row_times(const InnerArgs& A, int64_t a, int r0, const float* __restrict__ x,
+                                          float acc[12]) {
+  const int R = A.C.R;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = 0.f;
+  const int q0 = __ldg(A.rowptr + a), len = __ldg(A.rowptr + a + 1) - q0;
+  const int rr = (int)(a & 7);
+  const int64_t base = SLICED ? (int64_t)__ldg(A.sl_off + (a >> 3)) : 0;
+  for (int t = 0; t < len; ++t) {
+    int64_t b;
+    float m[9];
+    if (SLICED) {
+      const int64_t slot = base + t;
+      b = __ldg(A.sl_cols + slot * 8 + rr);
+      const float* Bk = A.sl_vals + slot * 72 + rr;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) m[k] = __ldg(Bk + 8 * k);
+    } else {
+      b = __ldg(A.cols + q0 + t);
+      const float* Bk = A.vals + 9 * (int64_t)(q0 + t);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) m[k] = __ldg(Bk + k);
+    }
+    // x was written by other CTAs earlier in this kernel: read through L2 (__ldcg),
+    // never from a line this SM's L1 may still hold from an earlier step
+    const float4* xb = reinterpret_cast<const float4*>(x + (b * R + r0) * 3);
+    const float4 v0 = __ldcg(xb), v1 = __ldcg(xb + 1), v2 = __ldcg(xb + 2);
+    const float v[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        acc[3 * w + i] += m[3 * i] * v[3 * w] + m[3 * i + 1] * v[3 * w + 1] + m[3 * i + 2] * v[3 * w + 2];
+  }
+}
+
+__device__ __forceinline__ void load12(const float* p, float v[12]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = q[0], b = q[1], c = q[2];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+}
+
+__device__ __forceinline__ void store12(float* p, const float v[12]) {
+  float4* q = reinterpret_cast<float4*>(p);
+  q[0] = make_float4(v[0], v[1], v[2], v[3]);
+  q[1] = make_float4(v[4], v[5], v[6], v[7]);
+  q[2] = make_float4(v[8], v[9], v[10], v[11]);
+}
+
+__device__ __forceinline__ void load_block(const float* __restrict__ Bi, int64_t a, float m[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = __ldg(Bi + 9 * a + k);
+}
+
+// adds a thread's 4-case partial sums (FP32, widened) of `nf` fields to the
+// per-parity global sums: warp shuffles over the lanes holding the same cases,
+// FP64 shared atomics per CTA, one FP64 global atomic per CTA, case and field
+template <int NF>
+__device__ __forceinline__ void reduce4(const InnerArgs& A, int r0, const float (&part)[NF][4], double* const (&out)[NF],
+                                        double* sm) {
+  const int R = A.C.R, G = R / 4;
+  for (int i = threadIdx.x; i < NF * R; i += blockDim.x) sm[i] = 0.0;
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double v = (double)part[f][c];
+      for (int off = 16; off >= G; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) < G) atomicAdd(sm + f * R + r0 + c, v);
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NF * R; i += blockDim.x) atomicAdd(out[i / R] + (i % R), sm[i]);
+}
+
+template <bool SLICED>
+__global__ void __launch_bounds__(256) k_inner_persistent(InnerArgs A) {
+  __shared__ double sm[3 * 32];
+  __shared__ float s_alpha[32], s_beta[32];
+  __shared__ double s_rhob[32], s_en2[32], s_rho[32];
+  __shared__ int s_go;
+  const Cases& C = A.C;
+  const int R = C.R, G = R / 4;
+  const int64_t items = A.N * G;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = (int)(gid % G) * 4;   // the same 4 cases in every pass (stride is a multiple of G)
+  const bool lead = blockIdx.x == 0;
+
+  // start: q = A ubar, e = rbar - q, ||e||^2 and (M^-1 e, e) (k_inner_resid)
+  {
+    float part[2][4] = {};
+    for (int64_t i = gid; i < items; i += stride) {
+      const int64_t a = i / G;
+      const int64_t o = (a * R + r0) * 3;
+      float q[12], rv[12], m[9];
+      row_times<SLICED>(A, a, r0, A.ub, q);
+      load12(A.rb + o, rv);
+      load_block(A.B, a, m);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float v[3] = {rv[3 * c] - q[3 * c], rv[3 * c + 1] - q[3 * c + 1], rv[3 * c + 2] - q[3 * c + 2]}, z[3];
+        rv[3 * c] = v[0];
+        rv[3 * c + 1] = v[1];
+        rv[3 * c + 2] = v[2];
+        mv3(m, v, z);
+        part[0][c] += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        part[1][c] += z[0] * v[0] + z[1] * v[1] + z[2] * v[2];
+      }
+      store12(A.eb + o, rv);
+    }
+    double* const out[2] = {acc_at(A, 0, A_EN2), acc_at(A, 0, A_RHO)};
+    reduce4<2>(A, r0, part, out, sm);
+  }
+  if (!grid_barrier(A)) return;
+
+  int step = 0;
+  for (;; ++step) {
+    const int par = step & 1;
+    // stop test and beta (s_inner_check)
+    if (threadIdx.x == 0) s_go = 0;
+    __syncthreads();
+    if (threadIdx.x < R) {
+      const int r = threadIdx.x;
+      const double rbn = C.D(A.f_rbn2, r);
+      const bool act = C.I(I_ACTIVE, r) && rbn > 0.0;
+      const double en2 = *(volatile double*)(acc_at(A, par, A_EN2) + r);
+      const double rho = *(volatile double*)(acc_at(A, par, A_RHO) + r);
+      if (act && !(en2 / rbn <= A.eps)) atomicOr(&s_go, 1);   // NaN counts as "not converged"
+      const double rhob = step > 0 ? s_rhob[r] : 0.0;
+      const double be = (step > 0 && rhob != 0.0 && act) ? rho / rhob : 0.0;
+      s_beta[r] = (float)be;
+      s_en2[r] = en2;
+      s_rho[r] = rho;
+      if (lead) {
+        C.D(D_BETAI, r) = be;
+        C.D(D_EN2, r) = en2;
+        C.D(D_RHOA, r) = rho;
+        C.D(D_GAMI, r) = 0.0;
+      }
+    }
+    __syncthreads();
+    const bool stop = !s_go || step >= A.n_inner;
+    if (stop) break;
+
+    // search direction: pbar = Mbar^-1 e + beta pbar (k_inner_p)
+    for (int64_t i = gid; i < items; i += stride) {
+      const int64_t a = i / G;
+      const int64_t o = (a * R + r0) * 3;
+      float e[12], p[12], m[9];
+      load12(A.eb + o, e);
+      load12(A.pb + o, p);
+      load_block(A.B, a, m);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float be = s_beta[r0 + c];
+        float z[3];
+        mv3(m, e + 3 * c, z);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[3 * c + k] = be != 0.f ? z[k] + be * p[3 * c + k] : z[k];
+      }
+      store12(A.pb + o, p);
+    }
+    if (!grid_barrier(A)) return;
+
+    // q = Abar pbar and gamma = (pbar, q); CTA 0 clears the sums the next steps add to
+    if (lead)
+      for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        acc_at(A, par, A_EN2)[i] = 0.0;
+        acc_at(A, par, A_RHO)[i] = 0.0;
+        acc_at(A, par ^ 1, A_GAM)[i] = 0.0;
+      }
+    {
+      float part[1][4] = {};
+      for (int64_t i = gid; i < items; i += stride) {
+        const int64_t a = i / G;
+        const int64_t o = (a * R + r0) * 3;
+        float q[12], p[12];
+        row_times<SLICED>(A, a, r0, A.pb, q);
+        store12(A.qb + o, q);
+        load12(A.pb + o, p);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[0][c] += p[3 * c] * q[3 * c] + p[3 * c + 1] * q[3 * c + 1] + p[3 * c + 2] * q[3 * c + 2];
+      }
+      double* const out[1] = {acc_at(A, par, A_GAM)};
+      reduce4<1>(A, r0, part, out, sm);
+    }
+    if (!grid_barrier(A)) return;
+
+    // alpha (s_inner_alpha)
+    if (threadIdx.x < R) {
+      const int r = threadIdx.x;
+      const double g = *(volatile double*)(acc_at(A, par, A_GAM) + r), rho = s_rho[r];
+      const bool ok = C.I(I_ACTIVE, r) && C.D(A.f_rbn2, r) > 0.0 && g > 0.0 && isfinite(g) && isfinite(rho);
+      const double al = ok ? rho / g : 0.0;
+      s_alpha[r] = (float)al;
+      s_rhob[r] = rho;
+      if (lead) {
+        C.D(D_GAMI, r) = g;
+        C.D(D_ALPHAI, r) = al;
+        C.D(D_RHOB, r) = rho;
+        if (C.I(I_ACTIVE, r)) C.I(A.f_count, r) += 1;
+      }
+    }
+    __syncthreads();
+
+    // e -= alpha q ; ubar += alpha p ; ||e||^2, (M^-1 e, e) (k_inner_update)
+    {
+      float part[2][4] = {};
+      for (int64_t i = gid; i < items; i += stride) {
+        const int64_t a = i / G;
+        const int64_t o = (a * R + r0) * 3;
+        float e[12], q[12], u[12], p[12], m[9];
+        load12(A.eb + o, e);
+        load12(A.qb + o, q);
+        load12(A.ub + o, u);
+        load12(A.pb + o, p);
+        load_block(A.B, a, m);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float al = s_alpha[r0 + c];
+          float v[3], z[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            v[k] = e[3 * c + k] - al * q[3 * c + k];
+            e[3 * c + k] = v[k];
+            u[3 * c + k] += al * p[3 * c + k];
+          }
+          mv3(m, v, z);
+          part[0][c] += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          part[1][c] += z[0] * v[0] + z[1] * v[1] + z[2] * v[2];
+        }
+        store12(A.eb + o, e);
+        store12(A.ub + o, u);
+      }
+      double* const out[2] = {acc_at(A, par ^ 1, A_EN2), acc_at(A, par ^ 1, A_RHO)};
+      reduce4<2>(A, r0, part, out, sm);
+    }
+    if (!grid_barrier(A)) return;
+  }
+  // the loop's end state, as the per-step kernels leave it
+  if (lead && threadIdx.x == 0) {
+    *C.done = 1;
+    C.step() = step + 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 struct Solve {
@@ -894,6 +1228,9 @@ struct Solve {
   }
 };
 
+constexpr size_t kPersSums = 2 * 3 * 64 * sizeof(double);   // [2][3][R <= 64]
+constexpr size_t kPersBytes = kPersSums + 64;               // + barrier count, generation, abort flag
+
 static SolverWork* get_work(fe_mesh* m, int R) {
   SolverWork* w = m->work;
   if (w && w->R == R) return w;
@@ -916,6 +1253,7 @@ static SolverWork* get_work(fe_mesh* m, int R) {
   w->tq.alloc((size_t)N * 3 * 8);
   w->d.alloc((size_t)D_COUNT * R * 8 + 64);
   w->i.alloc((size_t)I_COUNT * R * 4 + 64);
+  w->pers.alloc(kPersBytes);
   FE_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
   FE_CUDA(cudaStreamCreateWithFlags(&w->body, cudaStreamNonBlocking));
   FE_CUDA(cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming));
@@ -959,7 +1297,80 @@ static void inner_step(Solve& S, const Level& L, cudaGraphConditionalHandle loop
   S.scal(s_inner_check, L.n, L.eps, L.f_rbn2, loop, use_loop);
 }
 
+// the whole inner loop of an assembled level as one persistent cooperative kernel
+// (k_inner_persistent); false when it does not apply (level 0, level 1 element by
+// element, R not 4, 8, 16 or 32, or the caller asked for per-step launches)
+static bool inner_loop_persistent(Solve& S, const Level& L) {
+  const int R = S.R;
+  if (S.o.inner_kernel != 0 || L.level == 0 || (L.level == 1 && !S.assembled1)) return false;
+  if (R != 4 && R != 8 && R != 16 && R != 32) return false;
+  const Coarse& c = S.m->coarse;
+  InnerArgs A;
+  A.N = L.N;
+  A.C = S.C;
+  A.B = L.B;
+  A.rb = L.rb;
+  A.ub = L.ub;
+  A.eb = L.eb;
+  A.pb = L.pb;
+  A.qb = L.qb;
+  A.sl_off = nullptr;
+  A.sl_cols = nullptr;
+  A.sl_vals = nullptr;
+  if (L.level == 1) {
+    A.rowptr = c.rowptr.as<int32_t>();
+    A.cols = c.cols.as<int32_t>();
+    A.vals = c.vals32.as<float>();
+    if (c.sl_vals.ptr) {
+      A.sl_off = c.sl_off.as<int32_t>();
+      A.sl_cols = c.sl_cols.as<int32_t>();
+      A.sl_vals = c.sl_vals.as<float>();
+    }
+  } else {
+    A.rowptr = c.rowptr2.as<int32_t>();
+    A.cols = c.cols2.as<int32_t>();
+    A.vals = c.vals2_32.as<float>();
+  }
+  A.n_inner = L.n;
+  A.eps = L.eps;
+  A.f_rbn2 = L.f_rbn2;
+  A.f_count = L.f_count;
+  unsigned char* base = S.w->pers.as<unsigned char>();
+  A.acc = reinterpret_cast<double*>(base);
+  A.bar = reinterpret_cast<unsigned*>(base + kPersSums);
+  A.abort_flag = reinterpret_cast<int*>(base + kPersSums + 8);
+  A.status = S.m->dev_status.as<int>();
+  A.timeout = 1LL << 31;   // about one second at 2 GHz
+  const bool sliced = A.sl_vals != nullptr;
+  const void* fn = sliced ? (const void*)k_inner_persistent<true> : (const void*)k_inner_persistent<false>;
+  int per_sm = 0, sms = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S.m->device));
+  if (per_sm < 1) return false;
+  const int64_t items = L.N * (R / 4);
+  const int64_t need = (items + 255) / 256;
+  const int64_t cap = (int64_t)per_sm * sms;   // every CTA resident at once (a cooperative launch checks it)
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(need, cap));
+  FE_CUDA(cudaMemsetAsync(S.w->pers.ptr, 0, kPersBytes, S.s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = S.s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (sliced)
+    FE_CUDA(cudaLaunchKernelEx(&cfg, k_inner_persistent<true>, A));
+  else
+    FE_CUDA(cudaLaunchKernelEx(&cfg, k_inner_persistent<false>, A));
+  return true;
+}
+
 static void inner_loop(Solve& S, const Level& L) {
+  if (inner_loop_persistent(S, L)) return;
   level_apply(S, L, L.ub, L.qb, nullptr);
   S.vec_on(L.N, *L.g, k_inner_resid, L.B, (const float*)L.rb, (const float*)L.qb, L.eb);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1093,6 +1504,13 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
   S.R = R;
   S.N = m->n_nodes;
   S.C = Cases{w->d.as<double>(), w->i.as<int>(), w->i.as<int>() + I_COUNT * R, R};
+  DevBuf hist;   // CG coefficients of PCG64, when the caller asked for them
+  if (o.solver == FE_SOLVER_PCG64 && o.cg_coef && o.cg_coef_len > 0 && !many) {
+    hist.alloc((size_t)o.cg_coef_len * R * 2 * sizeof(double));
+    FE_CUDA(cudaMemsetAsync(hist.ptr, 0, hist.bytes, s));
+    S.C.hist = hist.as<double>();
+    S.C.hist_len = o.cg_coef_len;
+  }
   S.g = vgeom(S.N, R, sms);
   S.sm = (size_t)S.g.tpb * sizeof(double);
   S.s = s;
@@ -1275,6 +1693,7 @@ static fe_status run_solve(fe_mesh* m, int R, const double* f, double* u, const 
     }
     FE_CUDA(cudaMemcpyAsync(hi.data(), w->i.ptr, hi.size() * 4, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaMemcpyAsync(hd.data(), w->d.ptr, hd.size() * 8, cudaMemcpyDeviceToHost, s));
+    if (hist.ptr) FE_CUDA(cudaMemcpyAsync(o.cg_coef, hist.ptr, hist.bytes, cudaMemcpyDeviceToHost, s));
     int32_t dev_status = 0;   // a bounded device-side wait of an EBE kernel gave up during the solve
     FE_CUDA(cudaMemcpyAsync(&dev_status, m->dev_status.ptr, sizeof(dev_status), cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
@@ -1327,6 +1746,9 @@ static void check_opts(const fe_solve_opts& o) {
     FE_REQUIRE(o.eps_inner1 >= 0.0, "eps_inner1 must be >= 0");
     FE_REQUIRE(o.coarse_op >= 0 && o.coarse_op <= 2, "coarse_op must be 0, 1 or 2");
   }
+  FE_REQUIRE(o.cg_coef_len >= 0 && o.cg_coef_len <= (1 << 24) && (o.cg_coef_len == 0 || o.cg_coef != nullptr),
+             "cg_coef_len must lie in [0, 2^24], with cg_coef set when it is positive");
+  FE_REQUIRE(o.inner_kernel == 0 || o.inner_kernel == 1, "inner_kernel must be 0 or 1");
 }
 
 }  // namespace fe
@@ -1441,11 +1863,10 @@ extern "C" fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void
 // Allocation-free build of the block-Jacobi preconditioner.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// preconditioner: code recording a CUDA stream capture (cudaMalloc may block or
-// synchronise the device, which capture forbids), latency-critical loops that must
-// not take the allocator's lock, and processes whose device memory is already
-// reserved by another allocator's pool (a framework's caching allocator), where a
-// fresh cudaMalloc can fail mid-run. For them fe_block_jacobi_noalloc keeps its
+// preconditioner: latency-critical loops that must not take the allocator's lock,
+// and processes whose device memory is already reserved by another allocator's
+// pool (a framework's caching allocator), where a fresh cudaMalloc can fail
+// mid-run. The call synchronises its stream (it reads an error flag back). For them fe_block_jacobi_noalloc keeps its
 // scratch (the FP64 [N][9] accumulator of diagonal blocks, the FP32 copy of the
 // inverse the shared kernel also writes, and an error flag) in the fixed
 // file-scope array below instead of allocating it. Every GPU that loads this
@@ -1461,7 +1882,9 @@ constexpr size_t kNoAllocBytes = kNoAllocFlag + 256;               // about 13.5
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device ordinal, looked up once per
-// device (the host-side name of the array is only a stand-in, not a device address).
+// device (the host-side name of the array is only a stand-in, not a device address)
+// and kept for the life of the process; it does not survive a reset of the
+// device's primary context.
 static void* g_noalloc_addr[256];
 static std::mutex g_noalloc_mutex;
 

@@ -22,6 +22,7 @@ FE_SOLVER_PCG64, FE_SOLVER_FCG_MIXED, FE_SOLVER_FCG_MG, FE_SOLVER_FCG_AMG = 0, 1
 SOLVERS = {"pcg64": FE_SOLVER_PCG64, "fcg_mixed": FE_SOLVER_FCG_MIXED, "fcg_mg": FE_SOLVER_FCG_MG,
            "fcg_amg": FE_SOLVER_FCG_AMG}
 COARSE_OPS = {"auto": 0, "assembled": 1, "ebe": 2}
+INNER_KERNELS = {"persistent": 0, "steps": 1}
 EBE_DIRECT, EBE_TILED = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
@@ -34,7 +35,8 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply", "fe_coarse_restrict",
             "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
             "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info",
-            "fe_ebe_apply_host", "fe_mesh_device_status"]
+            "fe_ebe_apply_host", "fe_mesh_device_status", "fe_obs_create", "fe_obs_destroy", "fe_obs_apply",
+            "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots"]
 
 
 class FeError(RuntimeError):
@@ -48,7 +50,8 @@ class SolveOpts(ctypes.Structure):
                 ("n_inner", ctypes.c_int32), ("eps_inner", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("literal_beta", ctypes.c_int32), ("check_every", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("n_inner1", ctypes.c_int32), ("eps_inner1", ctypes.c_double), ("coarse_op", ctypes.c_int32),
-                ("n_inner2", ctypes.c_int32), ("eps_inner2", ctypes.c_double)]
+                ("n_inner2", ctypes.c_int32), ("eps_inner2", ctypes.c_double),
+                ("cg_coef", ctypes.c_void_p), ("cg_coef_len", ctypes.c_int32), ("inner_kernel", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -104,12 +107,20 @@ def load(path: Optional[str] = None):
     lib.fe_coarse_matrix_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]
     lib.fe_ebe_apply_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     lib.fe_mesh_device_status.argtypes = [_vp, _vp]
+    lib.fe_obs_create.argtypes = [_vp, _i64, _i32, _vp, _vp, ctypes.POINTER(_vp)]
+    lib.fe_obs_destroy.argtypes = [_vp]
+    lib.fe_obs_destroy.restype = None
+    lib.fe_obs_apply.argtypes = [_vp, _i32, _vp, _vp, _vp]
+    lib.fe_obs_adjoint.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp]
+    lib.fe_combine_cases.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
+    lib.fe_case_dots.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp]
     for name in ("fe_mesh_create", "fe_mesh_info", "fe_mesh_set_log_young", "fe_ebe_apply", "fe_ebe_set_variant",
                  "fe_ebe_get_variant", "fe_ebe_tune", "fe_pcg_solve", "fe_solve_many", "fe_block_jacobi",
                  "fe_block_jacobi_noalloc", "fe_adjoint_grad", "fe_coarse_info", "fe_ebe4_apply",
                  "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
                  "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
-                 "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host", "fe_mesh_device_status"):
+                 "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host", "fe_mesh_device_status",
+                 "fe_obs_create", "fe_obs_apply", "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -170,6 +181,7 @@ class Mesh:
                                 _stream_ptr(torch.device("cuda", self.device)), ctypes.byref(h))
         _check(st, "fe_mesh_create")
         self._h = h
+        self.log_young = None   # the moduli given at creation
         self.n_nodes, self.n_elem = N, E
         self.free = torch.from_numpy(free.astype(np.float64)).to(f"cuda:{self.device}")
 
@@ -263,13 +275,19 @@ class Mesh:
         torch = _torch()
         p = _dev_ptr(logE, torch.float64, (self.n_elem,), name="logE")
         _check(load().fe_mesh_set_log_young(self._h, p, self._stream()), "fe_mesh_set_log_young")
+        self.log_young = logE.detach().clone()   # the moduli the mesh holds now
 
     # ---- solvers --------------------------------------------------------
     def solve(self, f, u0=None, solver: str = "fcg_mixed", tol: float = 1e-8, max_outer: int = 20000,
               n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
               check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
-              n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True):
-        """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status)."""
+              n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True, cg_coef=None,
+              inner_kernel: str = "persistent"):
+        """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status).
+        cg_coef (solver "pcg64" only): a C-contiguous float64 numpy array [k, R, 2] that
+        receives (alpha, beta) of the first k CG iterations of every case.
+        inner_kernel: "persistent" (one cooperative kernel per inner loop on the assembled
+        levels 1 and 2) or "steps" (one launch per vector pass and scalar step)."""
         torch = _torch()
         R = int(f.shape[1])
         fp = _dev_ptr(f, torch.float64, (self.n_nodes, R, 3), name="f")
@@ -283,6 +301,12 @@ class Mesh:
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         o.coarse_op = COARSE_OPS[coarse_op]
         o.n_inner2, o.eps_inner2 = int(n_inner2), float(eps_inner2)
+        o.inner_kernel = INNER_KERNELS[inner_kernel]
+        if cg_coef is not None:
+            if not (isinstance(cg_coef, np.ndarray) and cg_coef.dtype == np.float64 and cg_coef.ndim == 3 and
+                    cg_coef.shape[1:] == (R, 2) and cg_coef.flags["C_CONTIGUOUS"]):
+                raise ValueError("cg_coef must be a C-contiguous float64 array [k, R, 2]")
+            o.cg_coef, o.cg_coef_len = cg_coef.ctypes.data, int(cg_coef.shape[0])
         stats = (SolveStats * R)()
         st = load().fe_pcg_solve(self._h, R, fp, up, ctypes.byref(o), stats, self._stream())
         out = [dict(outer=s.outer_iters, inner=s.inner_iters, inner1=s.inner1_iters, inner2=s.inner2_iters,
@@ -294,7 +318,8 @@ class Mesh:
     def solve_many(self, f_cases, R_slots: int = 0, solver: str = "fcg_mixed", tol: float = 1e-8,
                    max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
                    n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
-                   n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True):
+                   n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True,
+                   inner_kernel: str = "persistent"):
         """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
         in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
         torch = _torch()
@@ -309,6 +334,7 @@ class Mesh:
         o.n_inner1, o.eps_inner1 = int(n_inner1), float(eps_inner1)
         o.coarse_op = COARSE_OPS[coarse_op]
         o.n_inner2, o.eps_inner2 = int(n_inner2), float(eps_inner2)
+        o.inner_kernel = INNER_KERNELS[inner_kernel]
         stats = (SolveStats * n)()
         r_used = _i32()
         st = load().fe_solve_many(self._h, n, fp, ctypes.c_void_p(u.data_ptr()), int(R_slots), ctypes.byref(o),
@@ -449,3 +475,75 @@ class Mesh:
         _check(load().fe_adjoint_grad(self._h, R, up, lp, ctypes.c_void_p(g.data_ptr()), self._stream()),
                "fe_adjoint_grad")
         return g
+
+    def combine_cases(self, G, a):
+        """u [N, 3] = sum_r a[r] G[:, r, :] (fe_combine_cases), G float64 [N, R, 3], a float64 [R]."""
+        torch = _torch()
+        R = int(G.shape[1])
+        gp = _dev_ptr(G, torch.float64, (self.n_nodes, R, 3), name="G")
+        ap = _dev_ptr(a, torch.float64, (R,), name="a")
+        u = torch.empty((self.n_nodes, 3), dtype=torch.float64, device=G.device)
+        _check(load().fe_combine_cases(self._h, R, gp, ap, ctypes.c_void_p(u.data_ptr()), self._stream()),
+               "fe_combine_cases")
+        return u
+
+    def case_dots(self, f, lam):
+        """out[r] = (P f_r) . lam (fe_case_dots), f float64 [N, R, 3], lam float64 [N, 3]."""
+        torch = _torch()
+        R = int(f.shape[1])
+        fp = _dev_ptr(f, torch.float64, (self.n_nodes, R, 3), name="f")
+        lp = _dev_ptr(lam, torch.float64, (self.n_nodes, 3), name="lam")
+        out = torch.empty(R, dtype=torch.float64, device=f.device)
+        _check(load().fe_case_dots(self._h, R, fp, lp, ctypes.c_void_p(out.data_ptr()), self._stream()),
+               "fe_case_dots")
+        return out
+
+
+class Observation:
+    """Observation operator of libfe (fe_obs_*): u_obs[p] = sum_j w[p, j] u[node[p, j]]."""
+
+    def __init__(self, mesh: Mesh, node, weight):
+        node = np.ascontiguousarray(node, dtype=np.int32)
+        weight = np.ascontiguousarray(weight, dtype=np.float64)
+        if node.ndim != 2 or weight.shape != node.shape:
+            raise ValueError("node and weight must be [n_obs, n_per] arrays of one shape")
+        self.mesh = mesh
+        self.n_obs, self.n_per = int(node.shape[0]), int(node.shape[1])
+        h = ctypes.c_void_p()
+        _check(load().fe_obs_create(mesh._h, self.n_obs, self.n_per, node.ctypes.data, weight.ctypes.data,
+                                    ctypes.byref(h)), "fe_obs_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fe_obs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, u):
+        """u [N, 3] or [N, R, 3] -> [n_obs, 3] or [n_obs, R, 3]."""
+        torch = _torch()
+        v = u if u.dim() == 3 else u.reshape(u.shape[0], 1, 3)
+        R = int(v.shape[1])
+        up = _dev_ptr(v.contiguous(), torch.float64, (self.mesh.n_nodes, R, 3), name="u")
+        out = torch.empty((self.n_obs, R, 3), dtype=torch.float64, device=u.device)
+        _check(load().fe_obs_apply(self._h, R, up, ctypes.c_void_p(out.data_ptr()), self.mesh._stream()),
+               "fe_obs_apply")
+        return out if u.dim() == 3 else out[:, 0, :]
+
+    def adjoint(self, g):
+        """P Obs^T g: g [n_obs, 3] or [n_obs, R, 3] -> [N, 3] or [N, R, 3], zero on constrained DOFs."""
+        torch = _torch()
+        v = g if g.dim() == 3 else g.reshape(g.shape[0], 1, 3)
+        R = int(v.shape[1])
+        v = v.contiguous()
+        gp = _dev_ptr(v, torch.float64, (self.n_obs, R, 3), name="g")
+        out = torch.empty((self.mesh.n_nodes, R, 3), dtype=torch.float64, device=g.device)
+        _check(load().fe_obs_adjoint(self.mesh._h, self._h, R, gp, ctypes.c_void_p(out.data_ptr()),
+                                     self.mesh._stream()), "fe_obs_adjoint")
+        return out if g.dim() == 3 else out[:, 0, :]

@@ -68,3 +68,44 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT,
                        env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_shard_cases_partitions_every_case_once():
+    sys.path.insert(0, ROOT)
+    import bench
+    for n in (0, 1, 5, 96, 97):
+        for world in (1, 2, 3, 4, 8):
+            shards = [bench.shard_cases(n, world, r) for r in range(world)]
+            flat = [c for sh in shards for c in sh]
+            assert flat == list(range(n))                        # contiguous, in order, each case once
+            sizes = [len(sh) for sh in shards]
+            assert max(sizes) - min(sizes) <= 1 and sizes == sorted(sizes, reverse=True)
+    with pytest.raises(ValueError):
+        bench.shard_cases(4, 2, 2)
+
+
+def _sharded_rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # 7 cases over 2 ranks: rank 0 solves 4 in 40 ms, rank 1 solves 3 in 36 ms
+    mine = bench.shard_cases(7, world, rank)
+    rate, tmax, total = bench.aggregate_sharded(len(mine), 40.0 - 4.0 * rank, dist, "cpu")
+    gathered = [None] * world
+    dist.all_gather_object(gathered, {"cases": list(mine)})
+    with open(os.path.join(out_dir, "rank%d.json" % rank), "w") as f:
+        json.dump({"rate": rate, "tmax": tmax, "total": total, "cases": [g["cases"] for g in gathered]}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_aggregate_gloo_world_two(tmp_path):
+    import torch.multiprocessing as mp
+    mp.start_processes(_sharded_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, start_method="spawn")
+    for r in range(2):
+        res = json.loads((tmp_path / ("rank%d.json" % r)).read_text())
+        assert res["total"] == 7.0 and res["tmax"] == 40.0
+        assert res["rate"] == pytest.approx(7.0 / 40e-3)
+        assert res["cases"] == [[0, 1, 2, 3], [4, 5, 6]]

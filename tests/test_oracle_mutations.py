@@ -34,6 +34,12 @@ MUTANTS = {
     "adjoint_sign": ("    g[e] = -acc;", "    g[e] = acc;"),
     "aggregate_stragglers_to_last": ("    agg[n] = first[best];", "    agg[n] = (int32_t)(count - 1);"),
     "galerkin_column_aggregate": ("        const int32_t B = agg[b];", "        const int32_t B = agg[a];"),
+    "inner_literal_n_minus_1": ("  for (int step = 0; step < n_steps; ++step) {\n    dots_f32(N, R, eb, eb, en);",
+                                "  for (int step = 0; step < n_steps - 1; ++step) {\n    dots_f32(N, R, eb, eb, en);"),
+    "inner_ratio_unsquared": ("if (active[c] && rbn[c] > 0.0 && en[c] / rbn[c] > worst) worst = en[c] / rbn[c];",
+                              "if (active[c] && rbn[c] > 0.0 && sqrt(en[c] / rbn[c]) > worst) worst = sqrt(en[c] / rbn[c]);"),
+    "inner_max_over_all_cases": ("if (active[c] && rbn[c] > 0.0 && en[c] / rbn[c] > worst) worst = en[c] / rbn[c];",
+                                 "if (rbn[c] > 0.0 && en[c] / rbn[c] > worst) worst = en[c] / rbn[c];"),
     "block_jacobi_transposed": ("for (int j = 0; j < 3; ++j) A[i][j] = vals[9 * b + 3 * i + j];",
                                 "for (int j = 0; j < 3; ++j) A[i][j] = vals[9 * b + 3 * j + i] * (i == j ? 1.0 : 0.5);"),
 }
@@ -53,6 +59,17 @@ PINS = [
     lambda: pins.test_aggregation_is_a_partition_into_connected_aggregates(pins.make_tet4_levels()),
     lambda: pins.test_galerkin_aggregation_matrix_is_the_triple_product(pins.make_tet4_levels()),
 ]
+
+
+def _box8():
+    m = pins.mg.plain_box()
+    return m, oracle.assemble(m), pins.mg.plain_box_rhs(m)
+
+
+# pins of the inner loop of Algorithm 1(b)
+PINS += [lambda: pins.test_fcg_inner_loop_runs_n0_steps_when_eps_is_zero(_box8()),
+         lambda: pins.test_fcg_inner_stop_rule_is_on_the_squared_ratio(_box8()),
+         lambda: pins.test_fcg_inner_stop_ignores_converged_cases(_box8())]
 
 
 def _solver_pin():

@@ -408,6 +408,60 @@ def test_fcg_zero_inner_is_pcg(box8):
     assert rel[0] <= 1.5e-8
 
 
+def _block_jacobi_numpy(K):
+    """Inverse 3x3 diagonal blocks of the assembled K_bc, from scipy's matrix and
+    numpy's inverse (independent of the oracle's own block-Jacobi routine)."""
+    A = K.to_scipy().tocsr()
+    n = A.shape[0] // 3
+    return np.stack([np.linalg.inv(A[3 * i:3 * i + 3, 3 * i:3 * i + 3].toarray()) for i in range(n)]), A
+
+
+def test_fcg_inner_loop_runs_n0_steps_when_eps_is_zero(box8):
+    """Algorithm 1(b) with a zero tolerance never stops early: every outer iteration
+    runs exactly N_0 inner steps (the cap of 30, not the 29 of a literal 'i < N')."""
+    m, K, f = box8
+    for n0 in (30, 7):
+        u, outer, inner, rel = oracle.fcg_mixed(K, f, tol=1e-8, eps_inner=0.0, n_inner=n0)
+        assert rel[0] <= 1.5e-8
+        assert inner[0] == n0 * outer[0]
+
+
+def test_fcg_inner_stop_rule_is_on_the_squared_ratio(box8):
+    """The inner loop stops before a step once ||e||^2 / ||rbar||^2 <= eps (the squared
+    ratio of Algorithm 1(b)). In the first outer iteration (u = 0, rbar = f) the first
+    test sees e = f - K M^-1 f; rho0 = ||e|| / ||f|| is computed here from scipy's
+    matrix and numpy's block inverses. With eps between rho0^2 and rho0 the squared
+    and the unsquared rule disagree on whether any step runs."""
+    m, K, f = box8
+    Minv, A = _block_jacobi_numpy(K)
+    fv = f[:, 0, :]
+    e = fv.reshape(-1) - A @ np.einsum("nij,nj->ni", Minv, fv).reshape(-1)
+    rho0 = np.linalg.norm(e) / np.linalg.norm(fv)
+    assert 0.2 < rho0 < 0.9                      # margins for the two tolerances below
+    _, outer, inner, _ = oracle.fcg_mixed(K, f, tol=1e-8, max_outer=1, eps_inner=rho0 ** 1.5)
+    assert outer[0] == 1 and inner[0] == 0       # rho0^2 <= eps < rho0: no step
+    _, outer, inner, _ = oracle.fcg_mixed(K, f, tol=1e-8, max_outer=1, eps_inner=rho0 ** 2.5)
+    assert outer[0] == 1 and inner[0] >= 1       # eps < rho0^2: at least one step
+
+
+def test_fcg_inner_stop_ignores_converged_cases(box8):
+    """The inner stop rule takes the maximum over the cases still active: a case that
+    starts converged (initial guess = its direct solution, so its FP32 residual is
+    rounding noise with an inner ratio far above eps) does not change another case's
+    iteration counts or solution."""
+    m, K, f = box8
+    lx, ly, lz = m.lattice_shape()
+    fa = mg.double_couple(m, (lx // 2 - 4, ly // 2 + 2, lz // 2 + 3), 1e12)[:, None, :]
+    ua = oracle.direct_solve(K, fa)
+    u1, outer1, inner1, rel1 = oracle.fcg_mixed(K, f, tol=1e-8)
+    F = np.concatenate([f, fa], axis=1)
+    U0 = np.concatenate([np.zeros_like(f), ua], axis=1)
+    u2, outer2, inner2, rel2 = oracle.fcg_mixed(K, F, u0=U0, tol=1e-8)
+    assert outer2[1] == 0 and inner2[1] == 0 and rel2[1] <= 1e-8
+    assert outer2[0] == outer1[0] and inner2[0] == inner1[0]
+    assert np.array_equal(u2[:, 0], u1[:, 0])
+
+
 def test_batched_cases_betti_and_linearity(box8):
     m, K, f1 = box8
     lx, ly, lz = m.lattice_shape()

@@ -69,6 +69,77 @@ def test_fcg_mixed_plain_box(box8, use_graph):
     assert stats[0]["inner"] <= 30 * stats[0]["outer"]
 
 
+def _three_cases(m):
+    lx, ly, lz = m.lattice_shape()
+    f = mg.plain_box_rhs(m)
+    fa = mg.double_couple(m, (lx // 2 - 4, ly // 2 + 2, lz // 2 + 3), 1e12)[:, None, :]
+    fg = (np.tile(np.array([0.0, 0.0, -1e9]), (m.n_nodes, 1)) * m.free)[:, None, :]
+    return np.concatenate([f, fa, fg], axis=1)
+
+
+@pytest.mark.gpu
+def test_fcg_inner_counts_match_oracle(box8):
+    """Per-case outer and inner iteration counts of the GPU's Algorithm 1 (three
+    cases in one batch, the paper's loop settings) against the oracle's. The two
+    round differently (GPU atomics, per-block partial sums), so the counts may
+    differ by a step: margin 1 outer iteration and 10 % + 3 inner steps per case."""
+    m, K, M = box8
+    F = _three_cases(m)
+    _, stats, st = M.solve(cuda(F), solver="fcg_mixed", tol=1e-8)
+    assert st == 0
+    _, outer, inner, _ = oracle.fcg_mixed(K, F, tol=1e-8)
+    for c in range(3):
+        assert abs(stats[c]["outer"] - int(outer[c])) <= 1, (c, stats[c], outer, inner)
+        assert abs(stats[c]["inner"] - int(inner[c])) <= 0.1 * inner[c] + 3, (c, stats[c], outer, inner)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n0", [30, 7])
+def test_fcg_inner_loop_runs_n0_steps_when_eps_is_zero(box8, n0):
+    m, K, M = box8
+    F = _three_cases(m)
+    _, stats, st = M.solve(cuda(F), solver="fcg_mixed", tol=1e-8, eps_inner=0.0, n_inner=n0)
+    assert st == 0
+    for c in range(3):
+        assert stats[c]["inner"] == n0 * stats[c]["outer"], (c, stats[c])
+
+
+@pytest.mark.gpu
+def test_fcg_inner_stop_rule_is_on_the_squared_ratio(box8):
+    """As the oracle's pin: in the first outer iteration the inner loop takes no step
+    when rho0^2 <= eps < rho0 (rho0 = ||f - K M^-1 f|| / ||f|| from scipy and numpy),
+    and at least one when eps < rho0^2."""
+    m, K, M = box8
+    f = mg.plain_box_rhs(m)
+    A = K.to_scipy().tocsr()
+    Minv = np.stack([np.linalg.inv(A[3 * i:3 * i + 3, 3 * i:3 * i + 3].toarray()) for i in range(m.n_nodes)])
+    fv = f[:, 0, :]
+    rho0 = np.linalg.norm(fv.reshape(-1) - A @ np.einsum("nij,nj->ni", Minv, fv).reshape(-1)) / np.linalg.norm(fv)
+    _, s1, _ = M.solve(cuda(f), solver="fcg_mixed", tol=1e-8, max_outer=1, eps_inner=rho0 ** 1.5,
+                       raise_on_fail=False)
+    _, s2, _ = M.solve(cuda(f), solver="fcg_mixed", tol=1e-8, max_outer=1, eps_inner=rho0 ** 2.5,
+                       raise_on_fail=False)
+    assert s1[0]["outer"] == 1 and s1[0]["inner"] == 0
+    assert s2[0]["outer"] == 1 and s2[0]["inner"] >= 1
+
+
+@pytest.mark.gpu
+def test_fcg_inner_stop_ignores_converged_cases(box8):
+    """A case that starts converged (initial guess = its direct solution) leaves
+    another case's counts unchanged (the inner stop is judged over active cases);
+    one step of rounding slack for the GPU's atomic summation order."""
+    m, K, M = box8
+    F = _three_cases(m)[:, :2]
+    ua = oracle.direct_solve(K, F[:, 1:2])
+    _, s1, st1 = M.solve(cuda(F[:, :1]), solver="fcg_mixed", tol=1e-8)
+    U0 = np.concatenate([np.zeros_like(ua), ua], axis=1)
+    _, s2, st2 = M.solve(cuda(F), u0=cuda(U0), solver="fcg_mixed", tol=1e-8)
+    assert st1 == 0 and st2 == 0
+    assert s2[1]["outer"] == 0 and s2[1]["relres"] <= 1e-8
+    assert abs(s2[0]["outer"] - s1[0]["outer"]) <= 1
+    assert abs(s2[0]["inner"] - s1[0]["inner"]) <= 3
+
+
 @pytest.mark.gpu
 def test_fcg_zero_inner_steps_tracks_pcg(box8):
     m, K, M = box8

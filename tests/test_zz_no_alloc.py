@@ -1,8 +1,7 @@
 """fe_block_jacobi_noalloc: the block-Jacobi preconditioner built without any
-device allocation, for callers that cannot allocate where they need it (code
-recording a CUDA stream capture, latency-critical loops that must not take the
-allocator's lock, processes whose device memory is held by another allocator's
-pool). Its scratch is a fixed file-scope device array shared by every call, so
+device allocation, for callers that cannot allocate where they need it
+(latency-critical loops that must not take the allocator's lock, processes whose
+device memory is held by another allocator's pool). Its scratch is a fixed file-scope device array shared by every call, so
 the test checks two calls in a row (the second must not see the first's
 leftovers), a second mesh, and the size limit.
 
