@@ -93,9 +93,10 @@ typedef struct {
                             the Lanczos tridiagonal of M^-1 K, hence condition estimates */
   int32_t cg_coef_len;   /* iterations cg_coef holds */
   int32_t inner_kernel;  /* inner loops on the assembled levels 1 and 2 (R = 4, 8, 16 or 32):
-                            0 one persistent cooperative kernel per loop (default; its CTAs
-                            meet at grid-wide barriers with bounded waits, see FE_ETIMEOUT);
-                            1 one launch per vector pass and scalar step */
+                            1 one launch per vector pass and scalar step (default; the
+                            faster on GB300, the step being bound by its vector traffic);
+                            0 one persistent cooperative kernel per loop (its CTAs meet at
+                            grid-wide barriers with bounded waits, see FE_ETIMEOUT) */
 } fe_solve_opts;
 
 /* Per-case results of fe_pcg_solve. */
@@ -118,7 +119,7 @@ const char* fe_version(void);
 /* Fills opts with the defaults: FCG_MIXED, tol 1e-8, max_outer 20000, n_inner 30,
  * eps_inner 0.1, use_graph 1, literal_beta 0, check_every 1, n_inner1 300,
  * eps_inner1 0.05, n_inner2 3000, eps_inner2 0.025 (the paper's table of loop settings,
- * levels 0, 1 and 2), coarse_op 0, cg_coef NULL, cg_coef_len 0, inner_kernel 0. */
+ * levels 0, 1 and 2), coarse_op 0, cg_coef NULL, cg_coef_len 0, inner_kernel 1. */
 void fe_solve_opts_default(fe_solve_opts* opts);
 
 /*

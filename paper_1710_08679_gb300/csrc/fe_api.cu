@@ -336,7 +336,7 @@ void fe_solve_opts_default(fe_solve_opts* o) {
   o->eps_inner2 = 0.025;
   o->cg_coef = nullptr;
   o->cg_coef_len = 0;
-  o->inner_kernel = 0;
+  o->inner_kernel = 1;
 }
 
 fe_status fe_mesh_create(int64_t n_nodes, const double* coords, int64_t n_elem, const int32_t* conn,

@@ -979,11 +979,12 @@ __device__ __forceinline__ void load_block(const float* __restrict__ Bi, int64_t
   for (int k = 0; k < 9; ++k) m[k] = __ldg(Bi + 9 * a + k);
 }
 
-// adds a thread's 4-case partial sums (FP32, widened) of `nf` fields to the
-// per-parity global sums: warp shuffles over the lanes holding the same cases,
+// adds a thread's 4-case partial sums (FP32, widened) of NF consecutive fields
+// to the per-parity global sums at out[f R + r]: warp shuffles over the lanes
+// holding the same cases,
 // FP64 shared atomics per CTA, one FP64 global atomic per CTA, case and field
 template <int NF>
-__device__ __forceinline__ void reduce4(const InnerArgs& A, int r0, const float (&part)[NF][4], double* const (&out)[NF],
+__device__ __forceinline__ void reduce4(const InnerArgs& A, int r0, const float (&part)[NF][4], double* out,
                                         double* sm) {
   const int R = A.C.R, G = R / 4;
   for (int i = threadIdx.x; i < NF * R; i += blockDim.x) sm[i] = 0.0;
@@ -997,11 +998,13 @@ __device__ __forceinline__ void reduce4(const InnerArgs& A, int r0, const float 
       if ((threadIdx.x & 31) < G) atomicAdd(sm + f * R + r0 + c, v);
     }
   __syncthreads();
-  for (int i = threadIdx.x; i < NF * R; i += blockDim.x) atomicAdd(out[i / R] + (i % R), sm[i]);
+  for (int i = threadIdx.x; i < NF * R; i += blockDim.x) atomicAdd(out + i, sm[i]);
 }
 
+constexpr int kInnerThreads = 1024;   // one CTA per SM: fewer arrivals per grid barrier
+
 template <bool SLICED>
-__global__ void __launch_bounds__(256) k_inner_persistent(InnerArgs A) {
+__global__ void __launch_bounds__(kInnerThreads, 1) k_inner_persistent(InnerArgs A) {
   __shared__ double sm[3 * 32];
   __shared__ float s_alpha[32], s_beta[32];
   __shared__ double s_rhob[32], s_en2[32], s_rho[32];
@@ -1036,8 +1039,7 @@ __global__ void __launch_bounds__(256) k_inner_persistent(InnerArgs A) {
       }
       store12(A.eb + o, rv);
     }
-    double* const out[2] = {acc_at(A, 0, A_EN2), acc_at(A, 0, A_RHO)};
-    reduce4<2>(A, r0, part, out, sm);
+    reduce4<2>(A, r0, part, acc_at(A, 0, A_EN2), sm);   // EN2 and RHO are consecutive fields
   }
   if (!grid_barrier(A)) return;
 
@@ -1109,8 +1111,7 @@ __global__ void __launch_bounds__(256) k_inner_persistent(InnerArgs A) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) part[0][c] += p[3 * c] * q[3 * c] + p[3 * c + 1] * q[3 * c + 1] + p[3 * c + 2] * q[3 * c + 2];
       }
-      double* const out[1] = {acc_at(A, par, A_GAM)};
-      reduce4<1>(A, r0, part, out, sm);
+      reduce4<1>(A, r0, part, acc_at(A, par, A_GAM), sm);
     }
     if (!grid_barrier(A)) return;
 
@@ -1160,8 +1161,7 @@ __global__ void __launch_bounds__(256) k_inner_persistent(InnerArgs A) {
         store12(A.eb + o, e);
         store12(A.ub + o, u);
       }
-      double* const out[2] = {acc_at(A, par ^ 1, A_EN2), acc_at(A, par ^ 1, A_RHO)};
-      reduce4<2>(A, r0, part, out, sm);
+      reduce4<2>(A, r0, part, acc_at(A, par ^ 1, A_EN2), sm);
     }
     if (!grid_barrier(A)) return;
   }
@@ -1344,17 +1344,17 @@ static bool inner_loop_persistent(Solve& S, const Level& L) {
   const bool sliced = A.sl_vals != nullptr;
   const void* fn = sliced ? (const void*)k_inner_persistent<true> : (const void*)k_inner_persistent<false>;
   int per_sm = 0, sms = 0;
-  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kInnerThreads, 0));
   FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S.m->device));
   if (per_sm < 1) return false;
   const int64_t items = L.N * (R / 4);
-  const int64_t need = (items + 255) / 256;
+  const int64_t need = (items + kInnerThreads - 1) / kInnerThreads;
   const int64_t cap = (int64_t)per_sm * sms;   // every CTA resident at once (a cooperative launch checks it)
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(need, cap));
   FE_CUDA(cudaMemsetAsync(S.w->pers.ptr, 0, kPersBytes, S.s));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kInnerThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = S.s;
   cudaLaunchAttribute attr[1];

@@ -282,12 +282,12 @@ class Mesh:
               n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True, literal_beta: bool = False,
               check_every: int = 1, n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
               n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True, cg_coef=None,
-              inner_kernel: str = "persistent"):
+              inner_kernel: str = "steps"):
         """Solve K_bc u = f for f [N, R, 3] float64; returns (u, stats list, status).
         cg_coef (solver "pcg64" only): a C-contiguous float64 numpy array [k, R, 2] that
         receives (alpha, beta) of the first k CG iterations of every case.
-        inner_kernel: "persistent" (one cooperative kernel per inner loop on the assembled
-        levels 1 and 2) or "steps" (one launch per vector pass and scalar step)."""
+        inner_kernel: "steps" (one launch per vector pass and scalar step, the default) or
+        "persistent" (one cooperative kernel per inner loop on the assembled levels 1 and 2)."""
         torch = _torch()
         R = int(f.shape[1])
         fp = _dev_ptr(f, torch.float64, (self.n_nodes, R, 3), name="f")
@@ -319,7 +319,7 @@ class Mesh:
                    max_outer: int = 20000, n_inner: int = 30, eps_inner: float = 0.1, use_graph: bool = True,
                    n_inner1: int = 300, eps_inner1: float = 0.05, coarse_op: str = "auto",
                    n_inner2: int = 3000, eps_inner2: float = 0.025, raise_on_fail: bool = True,
-                   inner_kernel: str = "persistent"):
+                   inner_kernel: str = "steps"):
         """Solve for f_cases [n_cases, N, 3] (float64, case-major) with at most R_slots
         in flight (0 = from free memory); returns (u [n_cases, N, 3], stats, status, R_used)."""
         torch = _torch()

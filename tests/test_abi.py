@@ -35,7 +35,7 @@ def test_version_and_defaults():
     lib.fe_solve_opts_default(ctypes.byref(o))
     assert o.solver == fe.FE_SOLVER_FCG_MIXED and o.tol == 1e-8 and o.n_inner == 30 and o.eps_inner == 0.1
     assert o.n_inner1 == 300 and o.eps_inner1 == 0.05 and o.n_inner2 == 3000 and o.eps_inner2 == 0.025
-    assert o.coarse_op == 0 and not o.cg_coef and o.cg_coef_len == 0 and o.inner_kernel == 0
+    assert o.coarse_op == 0 and not o.cg_coef and o.cg_coef_len == 0 and o.inner_kernel == 1
 
 
 def _create(m, **over):

@@ -272,3 +272,59 @@ def test_set_log_young_rebuilds_coarse_preconditioner(meshes):
     x4 = mg.random_vectors(cm.vertex.size, 4, seed=18).astype(np.float32).astype(np.float64)
     y4 = M.coarse_apply(cuda(x4, torch.float32)).double().cpu().numpy()
     assert rel_l2(y4, oracle.spmv(K1, x4)) <= TOL32
+
+
+def _uneven_cases(m, R, seed):
+    """R right-hand sides of different scales and shapes (random loads on the free
+    DOFs), so that the cases converge at different outer iterations."""
+    F = mg.random_vectors(m.n_nodes, R, seed=seed) * m.free[:, None, :]
+    return F * (1e9 * 10.0 ** (np.arange(R) % 5))[None, :, None]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solver", ["fcg_mg", "fcg_amg"])
+@pytest.mark.parametrize("R", [4, 8, 16, 32])
+def test_persistent_inner_loop_matches_per_step_launches(meshes, solver, R):
+    """The level-1 (and level-2) inner loop as one cooperative kernel against the
+    same loop issued as one launch per vector pass: the same Algorithm 1(b)
+    arithmetic, so the same counts (up to the order of the FP64 atomic sums) and
+    solutions that agree with each other and with the oracle's direct solve."""
+    m, cm, M = meshes["crust9x5x4"]
+    F = _uneven_cases(m, R, seed=40 + R)
+    res = {}
+    for kind in ("persistent", "steps"):
+        u, stats, st = M.solve(cuda(F), solver=solver, tol=1e-8, inner_kernel=kind)
+        assert st == 0, (kind, stats)
+        M.device_status()                                # raises if a barrier wait ran out
+        res[kind] = (u.cpu().numpy(), stats)
+    (up, sp), (us, ss) = res["persistent"], res["steps"]
+    K = oracle.assemble(m)
+    ud = oracle.direct_solve(K, F)
+    for r in range(R):
+        assert sp[r]["relres"] <= 1e-8 and sp[r]["inner1"] > 0
+        assert abs(sp[r]["outer"] - ss[r]["outer"]) <= 1
+        assert abs(sp[r]["inner1"] - ss[r]["inner1"]) <= max(3, 0.05 * ss[r]["inner1"])
+        if solver == "fcg_amg":
+            assert sp[r]["inner2"] > 0 and abs(sp[r]["inner2"] - ss[r]["inner2"]) <= max(5, 0.05 * ss[r]["inner2"])
+        assert rel_l2(up[:, r], ud[:, r]) <= 1e-6
+        assert rel_l2(up[:, r], us[:, r]) <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["persistent", "steps"])
+@pytest.mark.parametrize("n1", [1, 7])
+def test_level1_loop_runs_n1_steps_when_eps1_is_zero(meshes, kind, n1):
+    """eps_inner1 = 0: the stop rule never holds, so every outer iteration runs
+    exactly n_inner1 level-1 steps for every active case (Algorithm 1(b) with
+    eps = 0), in the persistent kernel as in the per-step launches."""
+    m, cm, M = meshes["crust9x5x4"]
+    F = _uneven_cases(m, 8, seed=5)
+    F[:, 3] = 0.0                                     # a zero case stays inactive: no steps counted
+    u, stats, st = M.solve(cuda(F), solver="fcg_mg", tol=1e-8, eps_inner1=0.0, n_inner1=n1, inner_kernel=kind)
+    assert st == 0
+    for r in range(8):
+        if r == 3:
+            assert stats[r]["outer"] == 0 and stats[r]["inner1"] == 0
+        else:
+            assert stats[r]["relres"] <= 1e-8
+            assert stats[r]["inner1"] == n1 * stats[r]["outer"], (r, stats[r])

@@ -141,6 +141,22 @@ def test_float_float_many_tiles_and_scales(R):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("R,tile", [(32, 10), (16, 17), (8, 20), (2, 7)])
+def test_float_float_tile_sizes_and_ragged_tail(R, tile):
+    """Tiles with more element-case items than the CTA has threads (several
+    passes, the last partly idle) and tile sizes that leave a ragged last tile:
+    every output must land (FP64 bar, per case)."""
+    m, _ = mg.crust_block(shape=(9, 7, 5), h=1000.0, jitter=0.15, seed=8)
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, R, seed=41 + R)
+    y = run(M, x, torch.float64, 3, tile=tile)
+    y_ref = oracle.spmv(K, x)
+    for r in range(R):
+        assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("R", [4, 8, 16, 32])
 def test_paired_fp32_kernel_matches_oracle(mesh_pair, R):
     """Two cases per thread (r and r + R/2) in paired FP32 arithmetic: every case
@@ -327,7 +343,7 @@ def test_largest_case_count_R64(dtype):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", [0, 1, 2, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_fully_constrained_mesh_is_identity(variant):
     """Every DOF fixed: K_bc = I, so every kernel must return x exactly (the
     paired kernel computes FP32 products only)."""
@@ -335,7 +351,8 @@ def test_fully_constrained_mesh_is_identity(variant):
     from paper_1710_08679_gb300 import fe
     m = MESHES["box2"]()
     M = fe.Mesh(m.coords, m.conn, m.young, m.poisson, np.zeros_like(m.free))
-    for dtype in ((torch.float32,) if variant == 4 else (torch.float64, torch.float32)):
+    for dtype in ((torch.float32,) if variant == 4 else (torch.float64,) if variant == 3
+                  else (torch.float64, torch.float32)):
         x = torch.from_numpy(mg.random_vectors(m.n_nodes, 4, seed=9)).to(dtype)
         y = run(M, x.numpy().astype(np.float64), dtype, variant, tile=8)
         assert np.array_equal(y, x.double().numpy())
