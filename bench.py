@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
     ap.add_argument("--profile", action="store_true",
                     help="EBE timing only, kernel fixed by --variant/--tile (no tuning, e2e, sweep, solve, CPU)")
-    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather", "df", "x2", "colour", "ws"],
+    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather", "df", "x2", "colour", "ws", "dflean"],
                     help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
@@ -57,6 +57,8 @@ def parse():
                          "cpu_solves: the oracle's plain PCG timed on the host cores on the solve meshes")
     ap.add_argument("--cpu-solves-small", action="store_true", help="cpu_solves on 24x24x12 meshes (testing only)")
     ap.add_argument("--many-cases", type=int, default=96, help="cases of --workload many")
+    ap.add_argument("--fd-directions", type=int, default=10, help="random directions of the FD noise check "
+                    "of --workload adjoint")
     ap.add_argument("--many-plain", type=int, default=1, help="cases timed with the plain FP64 PCG")
     ap.add_argument("--solver", choices=["pcg64", "fcg_mixed", "fcg_mg", "fcg_amg"], default="fcg_mg",
                     help="solver of --workload solve")
@@ -323,7 +325,8 @@ def run_ours(args):
     M = fe.Mesh.from_mesh(m, device=torch.cuda.current_device())
     R = R_MAIN
     if args.profile:
-        M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2, "df": 3, "x2": 4, "colour": 5, "ws": 6}[args.variant], args.tile)
+        M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2, "df": 3, "x2": 4, "colour": 5, "ws": 6,
+                                    "dflean": 7}[args.variant], args.tile)
         tt = torch.float32 if args.dtype == "f32" else torch.float64
         x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R)).to("cuda", tt)
         y = torch.empty_like(x)
@@ -423,7 +426,8 @@ def run_ours(args):
                 n = 5 if dt == "f64" else 10
                 kv, kt = M.get_variant(RR, dt)
                 sweep[f"{dt}_R{RR}"] = {"GDOF_cases_per_s": 3.0 * N * RR / (ms / n * 1e-3) / 1e9,
-                                        "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df", 4: "gather-x2", 5: "colour", 6: "ws"}[kv],
+                                        "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df", 4: "gather-x2", 5: "colour", 6: "ws",
+                                                    7: "gather-df-lean"}[kv],
                                         "tile": kt}
                 del xx, yy
         out["ebe_sweep"] = sweep
@@ -903,6 +907,18 @@ def run_adjoint(args):
     fd = (adjoint.misfit(M, logE0 + h * ve, a + h * va, sources, obs, d, fine) -
           adjoint.misfit(M, logE0 - h * ve, a - h * va, sources, obs, d, fine)) / (2 * h)
     an = float(gf_logE @ ve + gf_a @ va)
+    # noise of J itself (solves to 1e-13; atomic summation order varies between runs)
+    # and the central-difference error over further random directions
+    Js = [adjoint.misfit(M, logE0, a, sources, obs, d, fine) for _ in range(5)]
+    fd_err = []
+    for v2 in mg.unit_directions(args.fd_directions, m.n_elem + 16, seed=5):
+        ve2, va2 = torch.from_numpy(v2[:m.n_elem]).cuda(), torch.from_numpy(v2[m.n_elem:]).cuda()
+        fd2 = (adjoint.misfit(M, logE0 + h * ve2, a + h * va2, sources, obs, d, fine) -
+               adjoint.misfit(M, logE0 - h * ve2, a - h * va2, sources, obs, d, fine)) / (2 * h)
+        fd_err.append(abs(float(gf_logE @ ve2 + gf_a @ va2) - fd2) / abs(J0f))
+    noise = {"J_spread_over_5_evaluations_rel": (max(Js) - min(Js)) / abs(J0f),
+             "fd_abs_error_rel_to_J": {"directions": len(fd_err), "max": max(fd_err) if fd_err else None,
+                                       "median": float(np.median(fd_err)) if fd_err else None}}
     print(json.dumps({"metric": "adjoint gradient evaluations/s (forward + adjoint solves + sensitivity kernel)",
                       "value": 1.0 / dt, "unit": "gradients/s", "seconds_per_gradient": dt, "n_gpus": 1,
                       "higher_is_better": True, "data": "synthetic",
@@ -911,7 +927,7 @@ def run_adjoint(args):
                                  "steps": steps},
                       "fd_check": {"directional_derivative": an, "central_difference": fd,
                                    "relative_difference": abs(an - fd) / max(abs(fd), 1e-300), "h": h,
-                                   "solver": "fcg_mixed", "solve_tol": 1e-13}}), flush=True)
+                                   "solver": "fcg_mixed", "solve_tol": 1e-13}, "fd_noise": noise}), flush=True)
 
 
 def run_one_solve(args):

@@ -236,7 +236,12 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *                  element geometry and sum each tile node's element slots into y
  *                  (one 16-byte atomic add per 4 values). Tiles are grown greedily
  *                  (each takes the element sharing most nodes with it), built per
- *                  (tile_elems, R) on first use. */
+ *                  (tile_elems, R) on first use;
+ *   FE_EBE_DF_LEAN FP64 products only (R in {2, 4, 8, 16, 32}): the float-float
+ *                  kernel with a register-light element routine (node values and
+ *                  geometry read from shared memory where they are used, outputs
+ *                  stored as they are formed) and one input stage, so that two
+ *                  blocks share an SM and hide each other's latency. */
 typedef enum {
   FE_EBE_DIRECT = 0,
   FE_EBE_TILED = 1,
@@ -244,7 +249,8 @@ typedef enum {
   FE_EBE_GATHER_DF = 3,
   FE_EBE_GATHER_X2 = 4,
   FE_EBE_COLOUR = 5,
-  FE_EBE_WS = 6
+  FE_EBE_WS = 6,
+  FE_EBE_DF_LEAN = 7
 } fe_ebe_variant;
 
 /*

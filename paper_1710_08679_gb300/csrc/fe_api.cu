@@ -510,11 +510,11 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
                    variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2 || variant == FE_EBE_COLOUR ||
-                   variant == FE_EBE_WS,
+                   variant == FE_EBE_WS || variant == FE_EBE_DF_LEAN,
                "unknown variant %d", variant);
     FE_REQUIRE(variant != FE_EBE_WS || (dtype == FE_F32 && ws_supported(R)),
                "the warp-specialised kernel computes FP32 products for R in {4, 8, 16, 32}");
-    FE_REQUIRE(variant != FE_EBE_GATHER_DF || (dtype == FE_F64 && df_supported(R)),
+    FE_REQUIRE((variant != FE_EBE_GATHER_DF && variant != FE_EBE_DF_LEAN) || (dtype == FE_F64 && df_supported(R)),
                "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
     FE_REQUIRE(variant != FE_EBE_GATHER_X2 || (dtype == FE_F32 && x2_supported(R)),
                "the paired-arithmetic kernel computes FP32 products for R in {4, 8, 16, 32}");
@@ -541,6 +541,9 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     if (variant != FE_EBE_TILED) ensure_geometry_buffer(m, dtype == FE_F32);
     if (variant == FE_EBE_GATHER_DF)
       FE_REQUIRE(df_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",
+                 tile_elems, R);
+    else if (variant == FE_EBE_DF_LEAN)
+      FE_REQUIRE(df_lean_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",
                  tile_elems, R);
     else if (variant == FE_EBE_GATHER_X2)
       FE_REQUIRE(x2_fits(m, tile_elems, R), "tile of %d elements does not fit in shared memory for R = %d",

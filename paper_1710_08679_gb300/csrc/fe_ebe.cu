@@ -1025,6 +1025,155 @@ __global__ void __launch_bounds__(kThreads) ebe_pipe_df_kernel(int64_t n_tiles, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Float-float kernel for two blocks per SM (FE_EBE_DF_LEAN). The tiles, packets,
+// split, slots and node sums of ebe_pipe_df_kernel, with
+//  * elem_apply_df_lean: node values and geometry read from shared memory where
+//    they are used and outputs stored as they are formed, so the product fits in
+//    128 registers per thread;
+//  * one input stage: the next tile's rows are copied while this tile's node
+//    sums run (they read only the slots), which halves that buffer.
+// Two 256-thread blocks per SM then overlap each other's phases (split, element
+// products, node sums) where the one-block kernel waits on its own latencies.
+// ---------------------------------------------------------------------------
+template <int R>
+__host__ __device__ size_t pipe_df_lean_smem_bytes(int nnmax, int te, int pk) {
+  using C = GatherCfg<double, R>;
+  return (size_t)3 * pk + (size_t)3 * te * kGeo * sizeof(df) + (size_t)nnmax * C::VR * sizeof(double) +
+         (size_t)te * C::S * sizeof(df) + (size_t)((te * 10 + 3) & ~3) * sizeof(int) + (size_t)te * 12 * sizeof(int);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads, 2) ebe_pipe_df_lean_kernel(int64_t n_tiles, int64_t n_elem, int te,
+                                                                       int nnmax,
+                                                                       const unsigned char* __restrict__ packets,
+                                                                       int pk, const df* __restrict__ geo,
+                                                                       const double* __restrict__ x,
+                                                                       double* __restrict__ y,
+                                                                       const int* __restrict__ skip) {
+  using C = GatherCfg<double, R>;
+  constexpr int VR = C::VR, S = C::S, CPN = VR / 2;   // 16-byte chunks of two values
+  static_assert(C::VEC, "float-float kernel needs 16-byte node rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (skip && *skip) return;
+  const PacketLayout L(nnmax, te);
+  unsigned char* meta = smem_raw;                                   // [3][pk]
+  df* geo_s = reinterpret_cast<df*>(meta + 3 * (size_t)pk);         // [3][te][16]
+  double* xd = reinterpret_cast<double*>(geo_s + 3 * (size_t)te * kGeo);  // [nnmax][VR], split in place
+  df* ob = reinterpret_cast<df*>(xd + (size_t)nnmax * VR);          // [te][S]
+  int* io = reinterpret_cast<int*>(ob + (size_t)te * S);            // [te*10]
+  int* no = io + ((te * 10 + 3) & ~3);                              // [te][12]
+  const int64_t G = gridDim.x;
+  int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+
+  auto issue_meta = [&](int64_t tile, int stage) {
+    const unsigned char* src = packets + tile * (int64_t)pk;
+    unsigned char* dst = meta + (size_t)stage * pk;
+    for (int k = threadIdx.x; k < pk / 16; k += blockDim.x) cp_async16(dst + 16 * k, src + 16 * k);
+    const int64_t rem = n_elem - tile * (int64_t)te;
+    const int ne = rem < (int64_t)te ? (int)rem : te;
+    const df* gsrc = geo + tile * (int64_t)te * kGeo;
+    df* gdst = geo_s + (size_t)stage * te * kGeo;
+    for (int k = threadIdx.x; k < ne * kGeo / 2; k += blockDim.x) cp_async16(gdst + 2 * k, gsrc + 2 * k);
+  };
+  auto issue_x = [&](int stage_meta) {
+    const unsigned char* mb = meta + (size_t)stage_meta * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      cp_async16(xd + ln * VR + 2 * q, x + (int64_t)ids[ln] * VR + 2 * q);
+    }
+  };
+
+  issue_meta(t, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue_x(0);
+  if (t + G < n_tiles) issue_meta(t + G, 1);
+  cp_async_commit();
+
+  for (int i = 0; t < n_tiles; ++i, t += G) {
+    const int ms = i % 3;
+    cp_async_wait_all();      // this tile's rows and the next tile's packet
+    __syncthreads();
+    const unsigned char* mb = meta + (size_t)ms * pk;
+    const int nn = reinterpret_cast<const int*>(mb)[0];
+    const int ne = reinterpret_cast<const int*>(mb)[1];
+    const int* ids = reinterpret_cast<const int*>(mb + L.ids);
+    const unsigned char* mks = mb + L.mask;
+    const unsigned char* own = mb + L.own;
+    const uint16_t* is = reinterpret_cast<const uint16_t*>(mb + L.inc_start);
+    const uint16_t* lc = reinterpret_cast<const uint16_t*>(mb + L.lconn);
+    const uint16_t* ic = reinterpret_cast<const uint16_t*>(mb + L.inc);
+    const df* gs = geo_s + (size_t)ms * te * kGeo;
+    df* xcur = reinterpret_cast<df*>(xd);
+    // split the inputs in place (P x: constrained components become zero)
+    for (int k = threadIdx.x; k < nn * VR; k += blockDim.x) {
+      const int ln = k / VR;
+      const int w = k - ln * VR;
+      const double v = xd[k];
+      xcur[k] = ((mks[ln] >> (w % 3)) & 1) ? df_split(v) : df(0.f, 0.f);
+    }
+    for (int j = threadIdx.x; j < ne * 10; j += blockDim.x) {
+      const int code = ic[j];
+      const int le = code / 10;
+      io[j] = le * S + (code - 10 * le) * VR;
+      const int e = j / 10;
+      no[e * 12 + (j - 10 * e)] = lc[j] * VR;
+    }
+    if (t + 2 * G < n_tiles) issue_meta(t + 2 * G, (i + 2) % 3);
+    cp_async_commit();
+    __syncthreads();
+
+    for (int it = threadIdx.x; it < ne * R; it += blockDim.x) {
+      const int le = it / R;
+      const int r = it - le * R;
+      int off[12];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int4 w = reinterpret_cast<const int4*>(no + le * 12)[q];
+        off[4 * q] = w.x;
+        off[4 * q + 1] = w.y;
+        off[4 * q + 2] = w.z;
+        off[4 * q + 3] = w.w;
+      }
+      elem_apply_df_lean<VR>(gs + le * kGeo, xcur + 3 * r, off, ob + le * S + 3 * r);
+    }
+    __syncthreads();
+    // the next tile's rows into the one input buffer while the node sums run
+    if (t + G < n_tiles) issue_x((i + 1) % 3);
+    cp_async_commit();
+
+    // node sums in float-float, converted to FP64 for the global atomic add
+    for (int k = threadIdx.x; k < nn * CPN; k += blockDim.x) {
+      const int ln = k / CPN;
+      const int q = k - ln * CPN;
+      df a0, a1;
+      const int j1 = is[ln + 1];
+      const df* obq = ob + 2 * q;
+      for (int j = is[ln]; j < j1; ++j) {
+        const float4 w = *reinterpret_cast<const float4*>(obq + io[j]);
+        a0 += df(w.x, w.y);
+        a1 += df(w.z, w.w);
+      }
+      const int64_t gi = (int64_t)ids[ln] * VR + 2 * q;
+      const int mk = mks[ln];
+      const df acc[2] = {a0, a1};
+#pragma unroll
+      for (int tt = 0; tt < 2; ++tt) {
+        if ((mk >> ((2 * q + tt) % 3)) & 1)
+          atomicAdd(y + gi + tt, df_to_double(acc[tt]));
+        else if (own[ln])
+          y[gi + tt] = __ldg(x + gi + tt);
+      }
+    }
+  }
+}
+
 template <typename T>
 size_t tiled_smem_bytes(int max_nodes, int tile_elems, int R) {
   size_t b = (size_t)max_nodes * 3 * R * sizeof(T) * 2 + (size_t)tile_elems * kGeo * sizeof(T) +
@@ -1172,6 +1321,40 @@ static bool launch_pipe_df(const fe_mesh* m, const Tiling& t, int R, const doubl
   }
 }
 
+template <int R>
+static bool launch_pipe_df_lean_r(const fe_mesh* m, const Tiling& t, const double* x, double* y, cudaStream_t s,
+                                  const int* skip) {
+  if (!m->geodf.ptr || t.packet_bytes == 0) return false;
+  const size_t smem = pipe_df_lean_smem_bytes<R>(t.max_nodes, t.tile_elems, t.packet_bytes);
+  if (smem > (size_t)max_smem_optin(m->device)) return false;
+  FE_CUDA(cudaFuncSetAttribute(ebe_pipe_df_lean_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_pipe_df_lean_kernel<R>, kThreads, smem));
+  FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+  if (per_sm < 1) return false;
+  const int64_t nv = m->n_nodes * (int64_t)R * 3;
+  prep_df_kernel<<<(unsigned)(sms * 8), kThreads, 0, s>>>(m->view<double>(), m->geodf.as<df>(), nv, y, skip);
+  FE_CHECK_LAUNCH();
+  const int64_t grid = std::min<int64_t>(t.n_tiles, (int64_t)per_sm * sms);
+  ebe_pipe_df_lean_kernel<R><<<(unsigned)grid, kThreads, smem, s>>>(
+      t.n_tiles, m->n_elem, t.tile_elems, t.max_nodes, t.packets.as<unsigned char>(), t.packet_bytes,
+      m->geodf.as<df>(), x, y, skip);
+  FE_CHECK_LAUNCH();
+  return true;
+}
+
+static bool launch_pipe_df_lean(const fe_mesh* m, const Tiling& t, int R, const double* x, double* y,
+                                cudaStream_t s, const int* skip) {
+  switch (R) {
+    case 2: return launch_pipe_df_lean_r<2>(m, t, x, y, s, skip);
+    case 4: return launch_pipe_df_lean_r<4>(m, t, x, y, s, skip);
+    case 8: return launch_pipe_df_lean_r<8>(m, t, x, y, s, skip);
+    case 16: return launch_pipe_df_lean_r<16>(m, t, x, y, s, skip);
+    case 32: return launch_pipe_df_lean_r<32>(m, t, x, y, s, skip);
+    default: return false;
+  }
+}
+
 // FP32 pipelined kernel with two cases per thread (paired arithmetic), R in {4, 8, 16, 32}
 static bool launch_pipe_x2(const fe_mesh* m, const Tiling& t, int R, const float* x, float* y, cudaStream_t s,
                            const int* skip) {
@@ -1268,10 +1451,11 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
   if (kind != FE_EBE_DIRECT) {
     auto it = m->tilings.find(tile);
     FE_REQUIRE(it != m->tilings.end(), "tiling of %d elements was not built", tile);
-    if (kind == FE_EBE_GATHER_DF) {
+    if (kind == FE_EBE_GATHER_DF || kind == FE_EBE_DF_LEAN) {
       if constexpr (sizeof(T) == 8) {
-        FE_REQUIRE(launch_pipe_df(m, *it->second, R, x, y, s, skip),
-                   "float-float kernel unavailable for R = %d with tiles of %d elements", R, tile);
+        const bool ok = kind == FE_EBE_GATHER_DF ? launch_pipe_df(m, *it->second, R, x, y, s, skip)
+                                                 : launch_pipe_df_lean(m, *it->second, R, x, y, s, skip);
+        FE_REQUIRE(ok, "float-float kernel unavailable for R = %d with tiles of %d elements", R, tile);
       } else {
         FE_REQUIRE(false, "the float-float kernel computes FP64 products only");
       }
@@ -1338,6 +1522,22 @@ bool df_fits(const fe_mesh* m, int tile_elems, int R) {
   return smem <= (size_t)max_smem_optin(m->device);
 }
 
+bool df_lean_fits(const fe_mesh* m, int tile_elems, int R) {
+  auto it = m->tilings.find(tile_elems);
+  if (it == m->tilings.end()) return false;
+  const Tiling& t = *it->second;
+  size_t smem;
+  switch (R) {
+    case 2: smem = pipe_df_lean_smem_bytes<2>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 4: smem = pipe_df_lean_smem_bytes<4>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 8: smem = pipe_df_lean_smem_bytes<8>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 16: smem = pipe_df_lean_smem_bytes<16>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    case 32: smem = pipe_df_lean_smem_bytes<32>(t.max_nodes, t.tile_elems, t.packet_bytes); break;
+    default: return false;
+  }
+  return smem <= (size_t)max_smem_optin(m->device);
+}
+
 template void ebe_apply<float>(const fe_mesh*, int, const float*, float*, cudaStream_t, const int*);
 template void ebe_apply<double>(const fe_mesh*, int, const double*, double*, cudaStream_t, const int*);
 
@@ -1366,7 +1566,10 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
     if (tiled_fits(m, te, R, sizeof(T) == 4, FE_EBE_TILED)) cands.push_back(FE_EBE_TILED * 65536 + te);
   if (sizeof(T) == 8 && df_supported(R))
     for (int te : {4, 8, 12, 16, 24})
-      if (tiled_fits(m, te, R, 0, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_DF * 65536 + te);
+      if (tiled_fits(m, te, R, 0, FE_EBE_GATHER)) {
+        cands.push_back(FE_EBE_GATHER_DF * 65536 + te);
+        cands.push_back(FE_EBE_DF_LEAN * 65536 + te);
+      }
   if (sizeof(T) == 4 && x2_supported(R))
     for (int te : {16, 24, 32, 48, 64, 96})
       if (tiled_fits(m, te, R, 1, FE_EBE_GATHER)) cands.push_back(FE_EBE_GATHER_X2 * 65536 + te);
@@ -1388,6 +1591,8 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
         if (!ws_fits(m, v % 65536, R)) continue;
       } else if (v / 65536 == FE_EBE_GATHER_DF) {
         if (!df_fits(m, v % 65536, R)) continue;
+      } else if (v / 65536 == FE_EBE_DF_LEAN) {
+        if (!df_lean_fits(m, v % 65536, R)) continue;
       } else if (v / 65536 == FE_EBE_GATHER_X2) {
         if (!x2_fits(m, v % 65536, R)) continue;
       } else if (!tiled_fits(m, v % 65536, R, sizeof(T) == 4, v / 65536)) {

@@ -177,4 +177,127 @@ __device__ __forceinline__ void elem_apply(const ElemGeo<df>& G, const df u[10][
   edge_out_df<2, 3>(s, G4, y);
 }
 
+// ---------------------------------------------------------------------------
+// The same product with little register state, for kernels that run two blocks
+// per SM: the node values (node a, component c) are read from shared memory at
+// xa[off[a] + c] where they are used, the element's 16 float-float values
+// (g[4][3], lam, mu, V/20) from gs, and the 30 outputs are stored to
+// o[a * VR + c] as they are formed. Same operations in the same order as
+// elem_apply above.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void corner_stress_df_lean(const df* gs, const df* xa, const int off[10], df s[6]) {
+  dfsum A[3][3];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    df v[3];
+    if (j == M) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[a] = dtimes3(xa[off[M] + a]);
+    } else {
+      const int e = (M == 0) ? (j == 1 ? 4 : j == 2 ? 6 : 7)
+                  : (M == 1) ? (j == 0 ? 4 : j == 2 ? 5 : 8)
+                  : (M == 2) ? (j == 0 ? 6 : j == 1 ? 5 : 9)
+                             : (j == 0 ? 7 : j == 1 ? 8 : 9);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[a] = dscale(xa[off[e] + a], 4.f) - xa[off[j] + a];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const df g = gs[3 * j + b];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (j == 0)
+          acc_first(A[a][b], v[a], g);
+        else
+          acc_add(A[a][b], v[a], g);
+      }
+    }
+  }
+  df H[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) H[a][b] = acc_value(A[a][b]);
+  const df lam = gs[12], mu = gs[13];
+  const df lt = lam * ((H[0][0] + H[1][1]) + H[2][2]);
+  const df two_mu = dscale(mu, 2.f);
+  s[0] = lt + two_mu * H[0][0];
+  s[1] = lt + two_mu * H[1][1];
+  s[2] = lt + two_mu * H[2][2];
+  s[3] = mu * (H[1][2] + H[2][1]);
+  s[4] = mu * (H[0][2] + H[2][0]);
+  s[5] = mu * (H[0][1] + H[1][0]);
+}
+
+// y_kl = T_k G4_l + T_l G4_k, stored to o[e VR + c]
+template <int K, int L, int VR>
+__device__ __forceinline__ void edge_out_df_lean(const df t[4][6], const df G4[4][3], df* o) {
+  constexpr int e = edge_node(K, L);
+  const df* a = t[K];
+  const df* b = t[L];
+  const df* g = G4[L];
+  const df* h = G4[K];
+  dfsum S;
+  acc_first(S, a[0], g[0]);
+  acc_add(S, a[5], g[1]);
+  acc_add(S, a[4], g[2]);
+  acc_add(S, b[0], h[0]);
+  acc_add(S, b[5], h[1]);
+  acc_add(S, b[4], h[2]);
+  o[e * VR] = acc_value(S);
+  acc_first(S, a[5], g[0]);
+  acc_add(S, a[1], g[1]);
+  acc_add(S, a[3], g[2]);
+  acc_add(S, b[5], h[0]);
+  acc_add(S, b[1], h[1]);
+  acc_add(S, b[3], h[2]);
+  o[e * VR + 1] = acc_value(S);
+  acc_first(S, a[4], g[0]);
+  acc_add(S, a[3], g[1]);
+  acc_add(S, a[2], g[2]);
+  acc_add(S, b[4], h[0]);
+  acc_add(S, b[3], h[1]);
+  acc_add(S, b[2], h[2]);
+  o[e * VR + 2] = acc_value(S);
+}
+
+template <int VR>
+__device__ __forceinline__ void elem_apply_df_lean(const df* gs, const df* xa, const int off[10], df* o) {
+  df s[4][6];
+  corner_stress_df_lean<0>(gs, xa, off, s[0]);
+  corner_stress_df_lean<1>(gs, xa, off, s[1]);
+  corner_stress_df_lean<2>(gs, xa, off, s[2]);
+  corner_stress_df_lean<3>(gs, xa, off, s[3]);
+  df S[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[q] = (s[0][q] + s[1][q]) + (s[2][q] + s[3][q]);
+  df G4[4][3];
+  const df c4 = dscale(gs[14], 4.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G4[k][i] = c4 * gs[3 * k + i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    df A[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) A[q] = s[k][q] - dscale(S[q], 0.25f);
+    df w[3];
+    sym_mv_df(A, G4[k], w);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[k * VR + c] = w[c];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s[k][q] += S[q];
+  edge_out_df_lean<0, 1, VR>(s, G4, o);
+  edge_out_df_lean<1, 2, VR>(s, G4, o);
+  edge_out_df_lean<0, 2, VR>(s, G4, o);
+  edge_out_df_lean<0, 3, VR>(s, G4, o);
+  edge_out_df_lean<1, 3, VR>(s, G4, o);
+  edge_out_df_lean<2, 3, VR>(s, G4, o);
+}
+
 }  // namespace fe

@@ -281,6 +281,7 @@ bool gather_supported(int R);
 void ensure_geometry_buffer(fe_mesh* m, int is_f32);
 bool df_supported(int R);
 bool df_fits(const fe_mesh* m, int tile_elems, int R);
+bool df_lean_fits(const fe_mesh* m, int tile_elems, int R);
 bool x2_supported(int R);
 bool x2_fits(const fe_mesh* m, int tile_elems, int R);
 const Tiling* get_tiling(fe_mesh* m, int tile_elems, cudaStream_t s);

@@ -113,15 +113,33 @@ def test_gather_many_tiles_per_cta(R, dtype):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("variant", [3, 7])
 @pytest.mark.parametrize("R", [2, 4, 16, 32])
-def test_float_float_fp64_kernel_matches_oracle(mesh_pair, R):
+def test_float_float_fp64_kernel_matches_oracle(mesh_pair, R, variant):
     """The FP64 product computed in float-float arithmetic on the FP32 pipe meets
-    the FP64 bar (1e-12)."""
+    the FP64 bar (1e-12), in the one-block and the two-blocks-per-SM kernel."""
     m, K, M = mesh_pair
     x = mg.random_vectors(m.n_nodes, R, seed=300 + R)
-    y = run(M, x, torch.float64, 3, tile=16)
-    assert M.get_variant(R, "f64")[0] == 3
+    y = run(M, x, torch.float64, variant, tile=16)
+    assert M.get_variant(R, "f64")[0] == variant
     assert rel_l2(y, oracle.spmv(K, x)) <= TOL64
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [4, 16])
+def test_float_float_kernels_agree(R):
+    """The lean element routine performs the same operations in the same order as
+    the one-block kernel's and the node sums add the slots in the same order, so
+    the two float-float kernels agree far below the FP64 bar at the same tile size
+    (not necessarily bitwise: the compiler may contract a product and a sum into
+    one FMA differently in the two)."""
+    m, _ = mg.crust_block(shape=(12, 10, 6), h=1000.0, jitter=0.15, seed=6)
+    M = gpu_mesh(m)
+    x = mg.random_vectors(m.n_nodes, R, seed=61 + R)
+    y3 = run(M, x, torch.float64, 3, tile=12)
+    y7 = run(M, x, torch.float64, 7, tile=12)
+    assert M.get_variant(R, "f64") == (7, 12)
+    assert rel_l2(y7, y3) <= 1e-15
 
 
 @pytest.mark.gpu
@@ -133,11 +151,12 @@ def test_float_float_many_tiles_and_scales(R):
     M = gpu_mesh(m)
     rng = np.random.default_rng(7)
     x = mg.random_vectors(m.n_nodes, R, seed=32) * 10.0 ** rng.uniform(-20, 20, size=(m.n_nodes, R, 1))
-    for tile in (4, 13):
-        y = run(M, x, torch.float64, 3, tile=tile)
-        y_ref = oracle.spmv(K, x)
-        for r in range(R):
-            assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
+    y_ref = oracle.spmv(K, x)
+    for variant in (3, 7):
+        for tile in (4, 13):
+            y = run(M, x, torch.float64, variant, tile=tile)
+            for r in range(R):
+                assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
 
 
 @pytest.mark.gpu
@@ -150,10 +169,11 @@ def test_float_float_tile_sizes_and_ragged_tail(R, tile):
     K = oracle.assemble(m)
     M = gpu_mesh(m)
     x = mg.random_vectors(m.n_nodes, R, seed=41 + R)
-    y = run(M, x, torch.float64, 3, tile=tile)
     y_ref = oracle.spmv(K, x)
-    for r in range(R):
-        assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
+    for variant in (3, 7):
+        y = run(M, x, torch.float64, variant, tile=tile)
+        for r in range(R):
+            assert rel_l2(y[:, r], y_ref[:, r]) <= TOL64
 
 
 @pytest.mark.gpu
@@ -343,7 +363,7 @@ def test_largest_case_count_R64(dtype):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7])
 def test_fully_constrained_mesh_is_identity(variant):
     """Every DOF fixed: K_bc = I, so every kernel must return x exactly (the
     paired kernel computes FP32 products only)."""
@@ -351,7 +371,7 @@ def test_fully_constrained_mesh_is_identity(variant):
     from paper_1710_08679_gb300 import fe
     m = MESHES["box2"]()
     M = fe.Mesh(m.coords, m.conn, m.young, m.poisson, np.zeros_like(m.free))
-    for dtype in ((torch.float32,) if variant == 4 else (torch.float64,) if variant == 3
+    for dtype in ((torch.float32,) if variant == 4 else (torch.float64,) if variant in (3, 7)
                   else (torch.float64, torch.float32)):
         x = torch.from_numpy(mg.random_vectors(m.n_nodes, 4, seed=9)).to(dtype)
         y = run(M, x.numpy().astype(np.float64), dtype, variant, tile=8)
