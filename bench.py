@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--shape", default=None, help="override mesh shape, e.g. 20x20x10 (testing only)")
     ap.add_argument("--profile", action="store_true",
                     help="EBE timing only, kernel fixed by --variant/--tile (no tuning, e2e, sweep, solve, CPU)")
-    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather", "df", "x2", "colour", "ws", "dflean"],
+    ap.add_argument("--variant", default="direct", choices=["direct", "tiled", "gather", "df", "x2", "colour", "ws", "dflean", "ws2"],
                     help="kernel for --profile (df: float-float FP64 kernel, --dtype f64 only)")
     ap.add_argument("--tile", type=int, default=48, help="elements per tile for --variant tiled")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision for --profile")
@@ -326,7 +326,7 @@ def run_ours(args):
     R = R_MAIN
     if args.profile:
         M.set_variant(R, args.dtype, {"direct": 0, "tiled": 1, "gather": 2, "df": 3, "x2": 4, "colour": 5, "ws": 6,
-                                    "dflean": 7}[args.variant], args.tile)
+                                    "dflean": 7, "ws2": 8}[args.variant], args.tile)
         tt = torch.float32 if args.dtype == "f32" else torch.float64
         x = torch.from_numpy(mg.random_vectors(N, R, seed=100 + R)).to("cuda", tt)
         y = torch.empty_like(x)
@@ -337,7 +337,7 @@ def run_ours(args):
     v32, us32 = M.tune(R, "f32")
     kind_name = {0: "direct", 1: "tiled", 2: "pipelined gather", 3: "gather-df",
                  4: "pipelined gather, two cases per thread in paired FP32", 5: "colour by colour",
-                 6: "warp-specialised"}[v32 // 65536]
+                 6: "warp-specialised", 7: "gather-df-lean", 8: "warp-specialised, two blocks per SM"}[v32 // 65536]
     kernel_desc = kind_name + ("" if v32 // 65536 in (0, 5) else " %d elements/tile" % (v32 % 65536))
     first_pass = "prep pass (element geometry, y = 0)" if v32 // 65536 in (2, 4) else "zero pass"
     # zero or prep pass + the kernel; the colour kernel launches once per colour
@@ -427,7 +427,7 @@ def run_ours(args):
                 kv, kt = M.get_variant(RR, dt)
                 sweep[f"{dt}_R{RR}"] = {"GDOF_cases_per_s": 3.0 * N * RR / (ms / n * 1e-3) / 1e9,
                                         "ms": ms / n, "variant": {0: "direct", 1: "tiled", 2: "gather", 3: "gather-df", 4: "gather-x2", 5: "colour", 6: "ws",
-                                                    7: "gather-df-lean"}[kv],
+                                                    7: "gather-df-lean", 8: "ws2"}[kv],
                                         "tile": kt}
                 del xx, yy
         out["ebe_sweep"] = sweep

@@ -241,7 +241,10 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *                  kernel with a register-light element routine (node values and
  *                  geometry read from shared memory where they are used, outputs
  *                  stored as they are formed) and one input stage, so that two
- *                  blocks share an SM and hide each other's latency. */
+ *                  blocks share an SM and hide each other's latency;
+ *   FE_EBE_WS2     FE_EBE_WS with 256-thread blocks, two per SM (at most 4 compute
+ *                  warps, so tile_elems * R / 2 in {32, 64, 96, 128}): each block's
+ *                  staging and compute phases fill the other's waits. */
 typedef enum {
   FE_EBE_DIRECT = 0,
   FE_EBE_TILED = 1,
@@ -250,7 +253,8 @@ typedef enum {
   FE_EBE_GATHER_X2 = 4,
   FE_EBE_COLOUR = 5,
   FE_EBE_WS = 6,
-  FE_EBE_DF_LEAN = 7
+  FE_EBE_DF_LEAN = 7,
+  FE_EBE_WS2 = 8
 } fe_ebe_variant;
 
 /*

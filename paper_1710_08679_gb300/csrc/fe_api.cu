@@ -510,9 +510,9 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
     FE_REQUIRE(R >= 1 && R <= 64, "R = %d out of range", R);
     FE_REQUIRE(variant == FE_EBE_DIRECT || variant == FE_EBE_TILED || variant == FE_EBE_GATHER ||
                    variant == FE_EBE_GATHER_DF || variant == FE_EBE_GATHER_X2 || variant == FE_EBE_COLOUR ||
-                   variant == FE_EBE_WS || variant == FE_EBE_DF_LEAN,
+                   variant == FE_EBE_WS || variant == FE_EBE_DF_LEAN || variant == FE_EBE_WS2,
                "unknown variant %d", variant);
-    FE_REQUIRE(variant != FE_EBE_WS || (dtype == FE_F32 && ws_supported(R)),
+    FE_REQUIRE((variant != FE_EBE_WS && variant != FE_EBE_WS2) || (dtype == FE_F32 && ws_supported(R)),
                "the warp-specialised kernel computes FP32 products for R in {4, 8, 16, 32}");
     FE_REQUIRE((variant != FE_EBE_GATHER_DF && variant != FE_EBE_DF_LEAN) || (dtype == FE_F64 && df_supported(R)),
                "the float-float kernel computes FP64 products for R in {2, 4, 8, 16, 32}");
@@ -528,11 +528,11 @@ fe_status fe_ebe_set_variant(fe_mesh* m, int32_t R, fe_dtype dtype, int32_t vari
       ebe_set_variant(m, R, dtype == FE_F32, FE_EBE_COLOUR * 65536 + m->colouring.n_colours);
       return;
     }
-    if (variant == FE_EBE_WS) {
+    if (variant == FE_EBE_WS || variant == FE_EBE_WS2) {
       FE_REQUIRE(tile_elems >= 1 && tile_elems <= 4096, "tile size %d out of range", tile_elems);
-      FE_REQUIRE(ws_fits(m, tile_elems, R), "warp-specialised tiles of %d elements do not fit for R = %d",
-                 tile_elems, R);
-      ebe_set_variant(m, R, 1, FE_EBE_WS * 65536 + tile_elems);
+      FE_REQUIRE(ws_fits(m, tile_elems, R, variant == FE_EBE_WS2 ? 256 : 512),
+                 "warp-specialised tiles of %d elements do not fit for R = %d", tile_elems, R);
+      ebe_set_variant(m, R, 1, variant * 65536 + tile_elems);
       return;
     }
     FE_REQUIRE(variant != FE_EBE_GATHER || gather_supported(R),

@@ -1436,13 +1436,13 @@ void ebe_apply(const fe_mesh* m, int R, const T* x, T* y, cudaStream_t s, const 
     launch_colour<T>(m, R, x, y, s, skip);
     return;
   }
-  if (kind == FE_EBE_WS) {
+  if (kind == FE_EBE_WS || kind == FE_EBE_WS2) {
     if constexpr (sizeof(T) == 4) {
       auto it = m->ws_tilings.find(tile * 256 + R);
       FE_REQUIRE(it != m->ws_tilings.end(), "warp-specialised tiling of %d elements for R = %d was not built", tile,
                  R);
       zero_pass<T>(m, R, y, s, skip);
-      launch_ws(m, *it->second, x, y, s, skip);
+      launch_ws(m, *it->second, x, y, s, skip, kind == FE_EBE_WS2 ? 256 : 512);
     } else {
       FE_REQUIRE(false, "the warp-specialised kernel computes FP32 products only");
     }
@@ -1576,6 +1576,9 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
   if (sizeof(T) == 4 && ws_supported(R))
     for (int items : {256, 320, 384, 448, 512})   // element-case items per tile: 4 to 8 compute warps
       if (items % R == 0) cands.push_back(FE_EBE_WS * 65536 + items / R);
+  if (sizeof(T) == 4 && ws_supported(R))
+    for (int items : {64, 128, 192, 256})         // two blocks per SM: 1 to 4 compute warps each
+      if (items % R == 0) cands.push_back(FE_EBE_WS2 * 65536 + items / R);
   cands.push_back(FE_EBE_COLOUR * 65536);  // the colour count is filled in once the colouring exists
   *best_variant = 0;
   *best_ms = 1e30f;
@@ -1586,9 +1589,9 @@ static void tune(fe_mesh* m, int R, cudaStream_t s, int* best_variant, float* be
       build_colouring(m, s);
       v = FE_EBE_COLOUR * 65536 + m->colouring.n_colours;
     } else if (v > 0) {
-      if (v / 65536 != FE_EBE_WS) get_tiling(m, v % 65536, s);
-      if (v / 65536 == FE_EBE_WS) {
-        if (!ws_fits(m, v % 65536, R)) continue;
+      if (v / 65536 != FE_EBE_WS && v / 65536 != FE_EBE_WS2) get_tiling(m, v % 65536, s);
+      if (v / 65536 == FE_EBE_WS || v / 65536 == FE_EBE_WS2) {
+        if (!ws_fits(m, v % 65536, R, v / 65536 == FE_EBE_WS2 ? 256 : 512)) continue;
       } else if (v / 65536 == FE_EBE_GATHER_DF) {
         if (!df_fits(m, v % 65536, R)) continue;
       } else if (v / 65536 == FE_EBE_DF_LEAN) {

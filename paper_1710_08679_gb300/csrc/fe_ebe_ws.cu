@@ -57,7 +57,8 @@ namespace fe {
 
 namespace {
 
-constexpr int kWsThreads = 512;   // 16 warps, one CTA per SM (128 registers per thread)
+constexpr int kWsThreads = 512;   // 16 warps, one CTA per SM (128 registers per thread); FE_EBE_WS2:
+                                  // half that, two CTAs per SM
 constexpr int kGeoWs = 40;        // floats of element data per element in shared memory
 constexpr int kPkSlots = 5;       // packets in shared memory (tiles i .. i + 4 of a staging iteration)
 
@@ -535,10 +536,9 @@ __device__ __forceinline__ void node_sums(const WsArgs& A, const Stg& c, int i, 
   }
 }
 
-template <int R>
+template <int R, int NT>
 __device__ __forceinline__ void ws_staging(const WsArgs& A, unsigned char* sm, const WsLayout& L, int n_it,
                                            int64_t t0, int64_t G, bool& ok) {
-  const int NT = kWsThreads;
   const uint32_t mb = smem_u32(sm);   // READY[s] at mb + 8 s, DONE[s] at mb + 16 + 8 s
   const int mt = threadIdx.x - A.cw * 32;
   const int NM = NT - A.cw * 32;
@@ -596,8 +596,8 @@ __device__ __forceinline__ void ws_staging(const WsArgs& A, unsigned char* sm, c
   cp_wait<0>();
 }
 
-template <int R>
-__global__ void __launch_bounds__(kWsThreads, 1) ebe_ws_kernel(const WsArgs A) {
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, kWsThreads / NT) ebe_ws_kernel(const WsArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
   if (A.skip && *A.skip) return;
   const int64_t G = gridDim.x, t0 = blockIdx.x;
@@ -606,8 +606,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) ebe_ws_kernel(const WsArgs A) {
   const WsLayout L(A.nnmax, A.nvmax, A.te);
   if (threadIdx.x == 0) {
     const uint32_t mb = smem_u32(sm);
-    mbar_init(mb, kWsThreads - 32 * A.cw);        // READY[0], READY[1]: every staging thread
-    mbar_init(mb + 8, kWsThreads - 32 * A.cw);
+    mbar_init(mb, NT - 32 * A.cw);                // READY[0], READY[1]: every staging thread
+    mbar_init(mb + 8, NT - 32 * A.cw);
     mbar_init(mb + 16, 32 * A.cw);                // DONE[0], DONE[1]: every compute thread
     mbar_init(mb + 24, 32 * A.cw);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ebe_ws_kernel(const WsArgs A) {
   if ((int)(threadIdx.x >> 5) < A.cw)
     ws_compute<R>(A, sm, L, n_it, ok);
   else
-    ws_staging<R>(A, sm, L, n_it, t0, G, ok);
+    ws_staging<R, NT>(A, sm, L, n_it, t0, G, ok);
 }
 
 // ---------------------------------------------------------------------------
@@ -856,17 +856,24 @@ static int max_smem_optin_ws(int device) {
   return v;
 }
 
-// The tiling fits when its buffers fit in shared memory.
-bool ws_fits(fe_mesh* m, int te, int R) {
-  if (!ws_supported(R)) return false;
+// The tiling fits when its buffers fit in shared memory and the block keeps at
+// least 4 staging warps (geometry, two loaders, node sums); 256-thread blocks
+// (two per SM) also need two blocks' buffers to fit in one SM.
+bool ws_fits(fe_mesh* m, int te, int R, int nth) {
+  if (!ws_supported(R) || (nth != kWsThreads && nth != kWsThreads / 2)) return false;
   const int cw = ws_compute_warps(te, R);
-  if (cw < 1 || cw > 12) return false;
+  if (cw < 1 || cw > nth / 32 - 4) return false;
   const WsTiling* t = get_ws_tiling(m, te, R, nullptr);
   const WsSmem sm(te, R, t->nnmax, t->pk_bytes);
-  return sm.bytes <= max_smem_optin_ws(m->device);
+  if (sm.bytes > max_smem_optin_ws(m->device)) return false;
+  if (nth == kWsThreads) return true;
+  int per_sm = 0, reserved = 0;
+  FE_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device));
+  FE_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device));
+  return 2 * (sm.bytes + reserved) <= per_sm;
 }
 
-template <int R>
+template <int R, int NT>
 static void launch_ws_r(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s,
                         const int* skip) {
   WsArgs A;
@@ -885,25 +892,37 @@ static void launch_ws_r(const fe_mesh* m, const WsTiling& t, const float* x, flo
   A.status = m->dev_status.as<int>();
   A.timeout = 1LL << 31;   // about one second at 2 GHz
   A.sm = WsSmem(t.te, R, t.nnmax, t.pk_bytes);
-  FE_REQUIRE(A.cw >= 1 && A.cw <= 12, "invalid tile size %d for R = %d", t.te, R);
+  FE_REQUIRE(A.cw >= 1 && A.cw <= NT / 32 - 4, "invalid tile size %d for R = %d with %d threads", t.te, R, NT);
   FE_REQUIRE(A.sm.bytes <= max_smem_optin_ws(m->device), "warp-specialised tile needs %d B of shared memory",
              A.sm.bytes);
-  FE_CUDA(cudaFuncSetAttribute(ebe_ws_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, A.sm.bytes));
-  int sms = 0;
+  FE_CUDA(cudaFuncSetAttribute(ebe_ws_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, A.sm.bytes));
+  int sms = 0, per_sm = 0;
   FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
-  const int64_t grid = std::min<int64_t>(t.n_tiles, sms);
-  ebe_ws_kernel<R><<<(unsigned)grid, kWsThreads, A.sm.bytes, s>>>(A);
+  FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ebe_ws_kernel<R, NT>, NT, A.sm.bytes));
+  FE_REQUIRE(per_sm >= 1, "warp-specialised kernel does not fit on an SM");
+  const int64_t grid = std::min<int64_t>(t.n_tiles, (int64_t)sms * std::min(per_sm, kWsThreads / NT));
+  ebe_ws_kernel<R, NT><<<(unsigned)grid, NT, A.sm.bytes, s>>>(A);
   FE_CHECK_LAUNCH();
 }
 
-void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip) {
+template <int NT>
+static void launch_ws_nt(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s,
+                         const int* skip) {
   switch (t.R) {
-    case 4: return launch_ws_r<4>(m, t, x, y, s, skip);
-    case 8: return launch_ws_r<8>(m, t, x, y, s, skip);
-    case 16: return launch_ws_r<16>(m, t, x, y, s, skip);
-    case 32: return launch_ws_r<32>(m, t, x, y, s, skip);
+    case 4: return launch_ws_r<4, NT>(m, t, x, y, s, skip);
+    case 8: return launch_ws_r<8, NT>(m, t, x, y, s, skip);
+    case 16: return launch_ws_r<16, NT>(m, t, x, y, s, skip);
+    case 32: return launch_ws_r<32, NT>(m, t, x, y, s, skip);
     default: FE_REQUIRE(false, "the warp-specialised kernel is built for R in {4, 8, 16, 32}, not %d", t.R);
   }
+}
+
+void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip,
+               int nth) {
+  if (nth == kWsThreads / 2)
+    launch_ws_nt<kWsThreads / 2>(m, t, x, y, s, skip);
+  else
+    launch_ws_nt<kWsThreads>(m, t, x, y, s, skip);
 }
 
 }  // namespace fe

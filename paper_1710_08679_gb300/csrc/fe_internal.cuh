@@ -292,8 +292,10 @@ bool tiled_fits(const fe_mesh* m, int tile_elems, int R, int is_f32, int kind);
 // Warp-specialised FP32 kernel (fe_ebe_ws.cu), R in {4, 8, 16, 32}
 bool ws_supported(int R);
 const WsTiling* get_ws_tiling(fe_mesh* m, int tile_elems, int R, cudaStream_t s);
-bool ws_fits(fe_mesh* m, int tile_elems, int R);
-void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip);
+// nth: threads per block, 512 (FE_EBE_WS, one block per SM) or 256 (FE_EBE_WS2, two)
+bool ws_fits(fe_mesh* m, int tile_elems, int R, int nth);
+void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip,
+               int nth);
 
 // Block Jacobi (fe_solver.cu)
 void build_block_jacobi(fe_mesh* m, cudaStream_t s);

@@ -17,7 +17,7 @@ from paper_1710_08679_gb300 import meshgen as mg
 torch = pytest.importorskip("torch")
 
 TOL32 = 2e-6
-WS = 6
+WS, WS2 = 6, 8     # 512-thread blocks (one per SM) and 256-thread blocks (two per SM)
 
 
 def gpu_mesh(m, free=None):
@@ -28,9 +28,9 @@ def gpu_mesh(m, free=None):
     return fe.Mesh(m.coords, m.conn, m.young, m.poisson, free)
 
 
-def ws_product(M, x, tile):
-    M.set_variant(x.shape[1], "f32", WS, tile)
-    assert M.get_variant(x.shape[1], "f32") == (WS, tile)
+def ws_product(M, x, tile, variant=WS):
+    M.set_variant(x.shape[1], "f32", variant, tile)
+    assert M.get_variant(x.shape[1], "f32") == (variant, tile)
     y = M.ebe(torch.from_numpy(x).to("cuda", torch.float32))
     M.device_status()   # no bounded wait of the kernel gave up
     return y.double().cpu().numpy()
@@ -193,3 +193,75 @@ def test_ws_full_size_crust_block_sampled_rows(R):
     assert rel_l2(y[nodes], ys) <= TOL32
     for r in range(R):
         assert rel_l2(y[nodes, r], ys[:, r]) <= TOL32, r
+
+
+# FE_EBE_WS2 (256-thread blocks, two per SM): one to four compute warps, i.e.
+# tile * R / 2 in {32, 64, 96, 128}, with two blocks' buffers in one SM's shared
+# memory (on the crust blocks that leaves three compute warps at most for
+# R = 16 and 32, and two for R = 4)
+WS2_SHAPES = [(16, 4), (16, 8), (16, 12), (4, 16), (4, 32), (8, 24), (32, 2), (32, 4), (32, 6), (8, 16)]
+TILE2 = {4: 32, 8: 16, 16: 12, 32: 6}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R", [4, 8, 16, 32])
+def test_ws2_kernel_matches_oracle_per_case(mesh_pair, R):
+    m, K, M = mesh_pair
+    x = fp32_vectors(m.n_nodes, R, 700 + R)
+    y = ws_product(M, x, TILE2[R], WS2)
+    ref = oracle.spmv(K, x)
+    for r in range(R):
+        assert rel_l2(y[:, r], ref[:, r]) <= TOL32, r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R,tile", WS2_SHAPES)
+def test_ws2_many_tiles_shapes_and_ragged_tail(crust20, R, tile):
+    m, K, M = crust20
+    x = fp32_vectors(m.n_nodes, R, 800 + R + tile)
+    y = ws_product(M, x, tile, WS2)
+    ref = oracle.spmv(K, x)
+    assert rel_l2(y, ref) <= TOL32
+    for r in (0, 1, R // 2, R - 1):
+        assert rel_l2(y[:, r], ref[:, r]) <= TOL32, r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("R,tile", [(16, 12), (4, 32), (32, 4), (8, 16)])
+def test_ws2_ragged_last_tile(R, tile):
+    """1,890 elements, not a multiple of 12, 32, 4 or 16: the last tile is short."""
+    m, _ = mg.crust_block(shape=(9, 7, 5), h=1000.0, jitter=0.15, seed=8)
+    K = oracle.assemble(m)
+    M = gpu_mesh(m)
+    x = fp32_vectors(m.n_nodes, R, 900 + R)
+    y = ws_product(M, x, tile, WS2)
+    ref = oracle.spmv(K, x)
+    for r in range(R):
+        assert rel_l2(y[:, r], ref[:, r]) <= TOL32, r
+
+
+@pytest.mark.gpu
+def test_ws2_constrained_repeated_and_identity():
+    """Constrained DOFs copy the input, ten products in a row agree, and a fully
+    constrained mesh is the identity, with two blocks per SM."""
+    m = MESHES["box2"]()
+    M = gpu_mesh(m)
+    x = fp32_vectors(m.n_nodes, 16, 6)
+    ys = [ws_product(M, x, 12, WS2) for _ in range(10)]
+    fixed = m.free == 0
+    for r in range(16):
+        assert np.array_equal(ys[0][:, r][fixed], x[:, r][fixed])
+    for y in ys[1:]:
+        assert rel_l2(y, ys[0]) <= 1e-6
+    Mf = gpu_mesh(m, free=np.zeros_like(m.free))
+    assert np.array_equal(ws_product(Mf, x, 12, WS2), x)
+
+
+@pytest.mark.gpu
+def test_ws2_rejects_more_than_four_compute_warps():
+    from paper_1710_08679_gb300 import fe
+    m = MESHES["box2"]()
+    M = gpu_mesh(m)
+    for R, tile in ((16, 20), (32, 10), (4, 80)):       # 5 compute warps: too many for 256 threads
+        with pytest.raises(fe.FeError):
+            M.set_variant(R, "f32", WS2, tile)
