@@ -231,12 +231,13 @@ fe_status fe_ebe_apply_host(fe_mesh* mesh, int32_t R, fe_dtype dtype, const void
  *   FE_EBE_WS      FP32 products only (R in {4, 8, 16, 32}; tile_elems * R / 2 a
  *                  multiple of 32, at most 384): warp-specialised kernel, one
  *                  block per SM. Compute warps evaluate two cases of an element per
- *                  thread in paired FP32 instructions; staging warps load the
- *                  following tiles' node values and coordinates, compute the
- *                  element geometry and sum each tile node's element slots into y
- *                  (one 16-byte atomic add per 4 values). Tiles are grown greedily
- *                  (each takes the element sharing most nodes with it), built per
- *                  (tile_elems, R) on first use;
+ *                  thread in paired FP32 instructions; staging warps bring in each
+ *                  tile's packet (node ids and coordinates, materials, offsets) with
+ *                  one bulk copy, load the tile's node values, compute the element
+ *                  geometry and sum each tile node's element slots into y (one
+ *                  16-byte atomic add per 4 values). Tiles are grown greedily (each
+ *                  takes the element sharing most nodes with it, up to a node
+ *                  budget), built per (tile_elems, R) on first use;
  *   FE_EBE_DF_LEAN FP64 products only (R in {2, 4, 8, 16, 32}): the float-float
  *                  kernel with a register-light element routine (node values and
  *                  geometry read from shared memory where they are used, outputs

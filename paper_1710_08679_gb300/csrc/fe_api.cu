@@ -291,6 +291,7 @@ static void upload_materials(fe_mesh* m, cudaStream_t s) {
   FE_CUDA(cudaMemcpyAsync(m->mat64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(m->mat32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice, s));
   FE_CUDA(cudaMemcpyAsync(m->matv.ptr, mv.data(), mv.size() * 4, cudaMemcpyHostToDevice, s));
+  fe::ws_refresh_materials(m, s);
   FE_CUDA(cudaStreamSynchronize(s));
   m->jacobi_ready = false;
   m->coarse.jacobi_ready = false;

@@ -1,51 +1,53 @@
 // Warp-specialised EBE product y = K_bc x in FP32 for R in {4, 8, 16, 32} cases
 // (Eq. 3, with the multiple vectors of Sec. 3.1).
 //
-// One CTA per SM walks its tiles t = blockIdx.x, + gridDim.x, ... Its warps take
-// one of two roles for the whole kernel:
+// One CTA per SM (FE_EBE_WS, 512 threads; FE_EBE_WS2: two 256-thread CTAs) walks its
+// tiles t = blockIdx.x, + gridDim.x, ... Its warps keep one role for the whole kernel:
 //  * compute warps: thread (element le, pair p) computes cases 2p and 2p + 1 of
 //    element le in paired FP32 instructions (elem_apply_ws), reading the element's
 //    node inputs (component-major rows) and geometry from shared memory and writing
 //    its 30 outputs per case to the element's own slot (no atomics inside the tile);
-//  * staging warps: copy the following tiles' node rows (in their global [case][comp]
-//    order, 16-byte cp.async, consecutive lanes on consecutive 16-byte chunks),
-//    coordinates, materials and index packets into shared memory ahead of use,
-//    transpose the rows to component-major order with the constrained components
-//    zeroed (P x), compute the element geometry (gradients of the volume
-//    coordinates and Lame constants: the element matrix is recomputed on every
-//    product, never stored), and, once the compute warps have finished a tile, sum
-//    every tile node's slots and add the sums into y with one 16-byte atomic add per
-//    4 values (owner tiles write (I - P) x on constrained components). The staging
-//    warps split this into three concurrent parts: warp 0 computes geometry, warps
-//    1 and 2 transpose rows and issue the copies, the others sum nodes. A node with
-//    more than kVnMax incidences in the tile is summed in pieces ("virtual nodes")
-//    of at most kVnMax incidences, each added into y on its own, so that every lane's
-//    loop is short and the summing warps are evenly loaded.
-// Two buffer sets ("stages") alternate between consecutive tiles. The roles hand
-// them over on mbarriers (waiting on one is not an arrival, so the compute warps do
-// not wait for one another and drift apart, overlapping one warp's loads with
-// another's arithmetic):
+//  * staging warps, in three roles that each run their own loop over the tiles:
+//      geometry (warp 0): gradients of the volume coordinates and Lame constants of
+//        every element of a tile from the packet's coordinates and materials (the
+//        element matrix is recomputed on every product, never stored);
+//      loaders (the next two or three warps): each tile node's row of x read from
+//        global memory into registers (48 contiguous bytes per thread and load),
+//        transposed to component-major order with constrained components zeroed
+//        (P x) and stored into the stage;
+//      node sums (the other warps): every tile node's slots summed and added into y
+//        with one 16-byte atomic add per 4 values (owner tiles write (I - P) x on
+//        constrained components). A node with more than kVnMax incidences in the tile
+//        is summed in pieces ("virtual nodes") of at most kVnMax incidences, each added
+//        into y on its own, so that lanes run short loops of similar length. The
+//        summing threads also issue the packet loads: one bulk copy (cp.async.bulk,
+//        completing on an mbarrier) per tile of its packet (node ids, coordinates,
+//        materials, offsets), npk tiles ahead.
+// Two buffer sets ("stages") alternate between consecutive tiles; the roles meet only
+// on mbarriers (waiting on one is not an arrival, so warps drift apart and overlap one
+// warp's loads with another's arithmetic):
 //   READY[s]  every staging thread arrives when stage s holds the inputs and
 //             geometry of tile i and the node sums of tile i - 2 (same slots) are
 //             done; the compute warps wait for it before tile i;
 //   DONE[s]   every compute thread arrives after its products of tile i; the staging
-//             warps wait for it before refilling stage s and summing tile i.
+//             warps wait for it before refilling stage s and summing tile i;
+//   PKF[k]    packet slot k holds its tile's packet (transaction bytes).
+// Before waiting for DONE, each staging role does the part of its work that needs
+// only packets: the loaders issue the global loads of tile i + 2's rows, the summing
+// threads read their first task's slot offsets, node id and mask, so that after DONE
+// only shared-memory stores, slot reads and atomics remain on the path to READY.
 // Each mbarrier wait is bounded (about one second of SM clock): a wait that gives
-// up records it in the mesh's device status word (fe_mesh_device_status) and the
-// kernel then runs to its end without waiting again, so no thread can hang.
-// Copies are waited with cp.async.wait_group and the staging warps meet at named
-// CTA barriers (hardware waits).
-// Per staging iteration i (after DONE[i]), concurrently: tile i + 2's geometry;
-// tile i + 2's rows (landed) transposed into stage s, then the rows, coordinates
-// and materials of tile i + 3 issued; tile i's node sums. Then the packet of tile
-// i + 5 is issued and READY[s] raised. y must be zero before the launch (the
-// caller's zero pass).
+// up records it in the mesh's device status word (fe_mesh_device_status), after
+// which the thread waits no more; before it exits, a thread that gave up waits (again
+// bounded) for the packet copies it may have left in flight. y must be zero before
+// the launch (the caller's zero pass).
 //
 // Tiles come from a greedy partition (get_ws_tiling): starting from the first
 // unassigned element in the mesh's locality order, a tile repeatedly takes the
 // unassigned element that shares the most nodes with it (ties: nearest to the
-// tile's centroid). Compact tiles have fewer nodes per element, hence fewer node
-// sums, input rows and global atomics per element-case product.
+// tile's centroid), up to te elements and a node budget. Compact tiles have fewer
+// nodes per element, hence fewer node sums, input rows and global atomics per
+// element-case product.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -60,14 +62,15 @@ namespace {
 constexpr int kWsThreads = 512;   // 16 warps, one CTA per SM (128 registers per thread); FE_EBE_WS2:
                                   // half that, two CTAs per SM
 constexpr int kGeoWs = 40;        // floats of element data per element in shared memory
-constexpr int kPkSlots = 5;       // packets in shared memory (tiles i .. i + 4 of a staging iteration)
-
-// named barriers (0 is __syncthreads); READY and DONE are mbarriers
-constexpr int kBarStaging = 1;    // all staging warps
-constexpr int kBarLoad = 2;       // the loader warps
-constexpr int kLoaderWarps = 2;   // staging warps 1 and 2
-constexpr int kVnMax = 8;         // incidences per virtual node (node-sum task)
-constexpr int kMbarBytes = 64;    // READY[2], DONE[2] at the start of shared memory
+constexpr int kPkMin = 4;         // packet slots in shared memory: at least (tiles i .. i + 3 are read)
+constexpr int kPkMax = 6;         // and at most
+constexpr int kBarSum = 1;        // named barrier of the node-sum warps (0 is __syncthreads)
+constexpr int kVnMax = 4;         // incidences per virtual node (node-sum task)
+// mbarriers at the start of shared memory (byte offsets)
+constexpr int kReady = 0;         // READY[2]
+constexpr int kDone = 16;         // DONE[2]
+constexpr int kPkf = 32;          // PKF[kPkMax]
+constexpr int kMbarBytes = 128;
 
 template <int R>
 struct WsCfg {
@@ -75,28 +78,34 @@ struct WsCfg {
   static constexpr int XR = 3 * R;                  // floats per node row
   static constexpr int S = 30 * R + (3 * R) % 32;   // slot stride per element: S = R (mod 32)
   static constexpr int G4 = R / 4;                  // node-sum lanes per node row (4 cases each)
-  static constexpr int CPN = 3 * R / 4;             // 16-byte chunks per node row
   static_assert(R % 4 == 0 && S % 4 == 0, "rows must stay 16-byte aligned");
 };
 
 __host__ __device__ constexpr int ws_slot_stride(int R) { return 30 * R + (3 * R) % 32; }
 __host__ __device__ constexpr int a16i(int b) { return (b + 15) & ~15; }
 
+// Node budget of a tile of te elements (the greedy tiler stops a tile that would
+// exceed it): bounds the shared memory of the row buffers.
+int ws_node_cap(int te) { return std::max(24, (11 * te) / 4 + 24); }
+
 }  // namespace
 
 // Byte layout of one packet (host and device agree on it); sections 16-byte aligned:
-//   int32 {nn, ne, nv, 0} | int32 ids[nnmax] (global node ids) | int32 elem[te]
-//   (internal element ids) | uint8 mask[nnmax] (free-DOF bits) | uint8 own[nnmax]
-//   (1 in the node's first tile) | uint32 vn[nvmax] (virtual nodes: local node in
-//   bits 0-11, first piece of its node in bit 12, incidence count in bits 13-16,
-//   first incidence in bits 17-31; longest first) | uint16 inc_off[10 te] (slot offset
-//   le S + a 3R of each element-node incidence, grouped by node) | uint16
+//   int32 {nn, ne, nv, 0} | float4 crd[nnmax] (node coordinates, FP32) | float4
+//   mat[te] (E, nu, 0, 0 per element) | int32 ids[nnmax] (global node ids) | int32
+//   elem[te] (internal element ids) | uint8 mask[nnmax] (free-DOF bits) | uint8
+//   own[nnmax] (1 in the node's first tile) | uint32 vn[nvmax] (virtual nodes: local
+//   node in bits 0-11, first piece of its node in bit 12, incidence count in bits
+//   13-16, first incidence in bits 17-31; longest first) | uint16 inc_off[10 te] (slot
+//   offset le S + a 3R of each element-node incidence, grouped by node) | uint16
 //   eoff[te][16] (0..9: row offset ln 3R of the element's nodes, 10..13: local ids of
 //   its corners, 14..15: 0)
 struct WsLayout {
-  int ids, elem, mask, own, vn, inc_off, eoff, bytes;
+  int crd, mat, ids, elem, mask, own, vn, inc_off, eoff, bytes;
   __host__ __device__ WsLayout(int nnmax, int nvmax, int te) {
-    ids = 16;
+    crd = 16;
+    mat = crd + 16 * nnmax;
+    ids = mat + 16 * te;
     elem = ids + a16i(4 * nnmax);
     mask = elem + a16i(4 * te);
     own = mask + a16i(nnmax);
@@ -107,18 +116,15 @@ struct WsLayout {
   }
 };
 
-// Shared-memory carve-up (bytes): mbarriers | packets [5][pk] | raw rows [nnmax][3R] (one tile,
-// global order) | coordinates [2][nnmax] float4 | materials [2][te] float4 |
-// xs [2][nnmax][3R] (component-major) | geo [2][te][40] | ob [2][te][S] (slots).
+// Shared-memory carve-up (bytes): mbarriers | packets [npk][pk] | xs [2][nnmax][3R]
+// (component-major node rows) | geo [2][te][40] | ob [2][te][S] (slots). Every
+// section is 16-byte aligned.
 struct WsSmem {
-  int pk = 0, raw = 0, crd = 0, mat = 0, xs = 0, geo = 0, ob = 0, bytes = 0;
+  int pk = 0, xs = 0, geo = 0, ob = 0, bytes = 0;
   WsSmem() = default;
-  __host__ __device__ WsSmem(int te, int R, int nnmax, int pkb) {
+  __host__ __device__ WsSmem(int te, int R, int nnmax, int pkb, int npk) {
     pk = kMbarBytes;
-    raw = pk + kPkSlots * pkb;
-    crd = raw + nnmax * 12 * R;
-    mat = crd + 2 * nnmax * 16;
-    xs = mat + 2 * te * 16;
+    xs = pk + npk * pkb;
     geo = xs + 2 * nnmax * 12 * R;
     ob = geo + 2 * te * kGeoWs * 4;
     bytes = ob + 2 * te * ws_slot_stride(R) * 4;
@@ -127,10 +133,9 @@ struct WsSmem {
 
 struct WsArgs {
   int64_t n_tiles;
-  int te, nnmax, nvmax, pk, cw;    // elements per tile, max nodes and virtual nodes, packet bytes, compute warps
+  int te, nnmax, nvmax, pk, npk, cw, nlw;   // elements per tile, max nodes and virtual nodes, packet
+                                            // bytes, packet slots, compute warps, loader warps
   const unsigned char* packets;
-  const float4* xyz4;              // [N] coordinates
-  const float4* matv;              // [E] (E, nu, 0, 0)
   const float* x;                  // [N][R][3]
   float* y;                        // [N][R][3], zero on entry
   const int* skip;
@@ -151,6 +156,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
+// arrival that also expects `bytes` of bulk-copy transactions in the current phase
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -160,8 +169,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of `bar` with parity `parity`, at most A.timeout cycles. A wait
-// that gives up records it in *A.status and clears ok, after which this thread waits
+// Waits for the phase of `bar` with parity `parity`, at most `timeout` cycles. A wait
+// that gives up records it in *status and clears ok, after which this thread waits
 // no more (the kernel then finishes; its results are flagged invalid).
 __device__ __forceinline__ void mbar_wait(int* status, long long timeout, uint32_t bar, uint32_t parity, bool& ok) {
   if (!ok || mbar_try(bar, parity)) return;
@@ -174,13 +183,22 @@ __device__ __forceinline__ void mbar_wait(int* status, long long timeout, uint32
     }
   }
 }
-__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+// bounded wait used only after a wait gave up: drains a bulk copy that may be in flight
+__device__ __forceinline__ void mbar_drain(long long timeout, uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity) && clock64() - t0 <= timeout) {
+  }
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// global -> this CTA's shared memory, completion counted on `bar` (addresses 16-byte
+// aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// orders this thread's earlier shared-memory accesses before later bulk copies into them
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ float2 b2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -278,21 +296,26 @@ __device__ __forceinline__ void elem_apply_ws(const float gv[kGeoWs], const floa
 // ---------------------------------------------------------------------------
 // compute warps
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ const unsigned char* pk_at(const WsArgs& A, const unsigned char* sm, int i) {
+  return sm + A.sm.pk + (i % A.npk) * A.pk;
+}
+
 template <int R>
 __device__ __forceinline__ void ws_compute(const WsArgs& A, unsigned char* sm, const WsLayout& L, int n_it,
                                            bool& ok) {
   using C = WsCfg<R>;
-  const uint32_t mb = smem_u32(sm);   // READY[s] at mb + 8 s, DONE[s] at mb + 16 + 8 s
+  const uint32_t mb = smem_u32(sm);
   const int le = threadIdx.x / C::RC, p = threadIdx.x - le * C::RC;
   const float* xs = reinterpret_cast<const float*>(sm + A.sm.xs);
   const float* geo = reinterpret_cast<const float*>(sm + A.sm.geo);
   float* ob = reinterpret_cast<float*>(sm + A.sm.ob);
   for (int i = 0; i < n_it; ++i) {
     const int st = i & 1;
-    mbar_wait(A.status, A.timeout, mb + 8 * st, (uint32_t)((i >> 1) & 1), ok);
-    const unsigned char* pk = sm + A.sm.pk + (i % kPkSlots) * A.pk;
+    mbar_wait(A.status, A.timeout, mb + kReady + 8 * st, (uint32_t)((i >> 1) & 1), ok);
+    const unsigned char* pk = pk_at(A, sm, i);
     const int ne = reinterpret_cast<const int*>(pk)[1];
-    if (le < ne) {
+    bool work = le < ne;
+    if (work) {
       const uint16_t* eo = reinterpret_cast<const uint16_t*>(pk + L.eoff) + le * 16;
       const uint4 w0 = *reinterpret_cast<const uint4*>(eo);
       const unsigned w1 = *reinterpret_cast<const unsigned*>(eo + 8);
@@ -323,55 +346,13 @@ __device__ __forceinline__ void ws_compute(const WsArgs& A, unsigned char* sm, c
 #pragma unroll
         for (int k = 0; k < 3; ++k) *reinterpret_cast<float2*>(o + a * C::XR + k * R) = yv[a][k];
     }
-    mbar_arrive(mb + 16 + 8 * st);
+    mbar_arrive(mb + kDone + 8 * st);
   }
 }
 
 // ---------------------------------------------------------------------------
 // staging warps
 // ---------------------------------------------------------------------------
-struct Stg {
-  unsigned char* sm;
-  WsLayout L;
-  int n_it, mt, NM;
-  int64_t t0, G;
-  __device__ unsigned char* pk(const WsArgs& A, int i) const { return sm + A.sm.pk + (i % kPkSlots) * A.pk; }
-  __device__ int64_t tile(int i) const { return t0 + (int64_t)i * G; }
-};
-
-__device__ __forceinline__ void issue_packet(const WsArgs& A, const Stg& c, int i) {
-  const unsigned char* src = A.packets + c.tile(i) * (int64_t)A.pk;
-  unsigned char* dst = c.pk(A, i);
-  for (int k = c.mt; k < A.pk / 16; k += c.NM) cp16(dst + 16 * k, src + 16 * k);
-}
-
-// rows of tile i -> raw (global order), consecutive lanes on consecutive chunks
-template <int R>
-__device__ __forceinline__ void issue_rows(const WsArgs& A, const Stg& c, int i) {
-  using C = WsCfg<R>;
-  const unsigned char* pk = c.pk(A, i);
-  const int nn = reinterpret_cast<const int*>(pk)[0];
-  const int* ids = reinterpret_cast<const int*>(pk + c.L.ids);
-  float* raw = reinterpret_cast<float*>(c.sm + A.sm.raw);
-  for (int k = c.mt; k < nn * C::CPN; k += c.NM) {
-    const int ln = k / C::CPN, q = k - ln * C::CPN;
-    cp16(raw + ln * C::XR + 4 * q, A.x + (int64_t)ids[ln] * C::XR + 4 * q);
-  }
-}
-
-// coordinates and materials of tile i -> buffer set b
-__device__ __forceinline__ void issue_geo_inputs(const WsArgs& A, const Stg& c, int i, int b) {
-  const unsigned char* pk = c.pk(A, i);
-  const int nn = reinterpret_cast<const int*>(pk)[0];
-  const int ne = reinterpret_cast<const int*>(pk)[1];
-  const int* ids = reinterpret_cast<const int*>(pk + c.L.ids);
-  const int* el = reinterpret_cast<const int*>(pk + c.L.elem);
-  float4* crd = reinterpret_cast<float4*>(c.sm + A.sm.crd) + (size_t)b * A.nnmax;
-  float4* mat = reinterpret_cast<float4*>(c.sm + A.sm.mat) + (size_t)b * A.te;
-  for (int k = c.mt; k < nn; k += c.NM) cp16(crd + k, A.xyz4 + ids[k]);
-  for (int k = c.mt; k < ne; k += c.NM) cp16(mat + k, A.matv + el[k]);
-}
-
 // node row of one 4-case group, [case][comp] -> component-major [comp][case], P x
 template <int R>
 __device__ __forceinline__ void put_row(float* xs_st, int ln, int g, int mk, const float4 v[3]) {
@@ -389,216 +370,298 @@ __device__ __forceinline__ void put_row(float* xs_st, int ln, int g, int mk, con
   for (int k = 0; k < 3; ++k) *reinterpret_cast<float4*>(d + k * R) = w[k];
 }
 
-// raw rows of tile i -> stage st
+// Node rows of a tile from x into a stage, split in two so that the global loads can
+// be in flight while the stage is still in use: rows_fetch loads the tasks k0, k0 + nl,
+// ... (kLdBatch of them) of loader thread k0 into registers, rows_put transposes and
+// stores them. Task (local node, group of 4 cases) = 48 contiguous bytes of x;
+// consecutive lanes take consecutive groups.
+constexpr int kLdBatch = 5;
 template <int R>
-__device__ __forceinline__ void transpose_rows(const WsArgs& A, const Stg& c, int i, int st) {
+__device__ __forceinline__ void rows_fetch(const WsArgs& A, const unsigned char* pk, const WsLayout& L, int k0, int nl,
+                                           float4 (&v)[kLdBatch][3]) {
   using C = WsCfg<R>;
-  const unsigned char* pk = c.pk(A, i);
-  const int nn = reinterpret_cast<const int*>(pk)[0];
-  const unsigned char* mks = pk + c.L.mask;
-  const float* raw = reinterpret_cast<const float*>(c.sm + A.sm.raw);
-  float* xs_st = reinterpret_cast<float*>(c.sm + A.sm.xs) + (size_t)st * A.nnmax * C::XR;
-  for (int k = c.mt; k < nn * C::G4; k += c.NM) {
-    const int ln = k / C::G4, g = k - ln * C::G4;
-    const float4* src = reinterpret_cast<const float4*>(raw + ln * C::XR) + 3 * g;
-    const float4 v[3] = {src[0], src[1], src[2]};
-    put_row<R>(xs_st, ln, g, mks[ln], v);
+  const int ntask = reinterpret_cast<const int*>(pk)[0] * C::G4;
+  const int* ids = reinterpret_cast<const int*>(pk + L.ids);
+#pragma unroll
+  for (int b = 0; b < kLdBatch; ++b) {
+    const int k = k0 + b * nl;
+    if (k < ntask) {
+      const int ln = k / C::G4, g = k - ln * C::G4;
+      const float4* src = reinterpret_cast<const float4*>(A.x + (int64_t)ids[ln] * C::XR) + 3 * g;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[b][q] = __ldcg(src + q);
+    }
+  }
+}
+template <int R>
+__device__ __forceinline__ void rows_put(const WsArgs& A, unsigned char* sm, const unsigned char* pk, const WsLayout& L,
+                                         int st, int k0, int nl, const float4 (&v)[kLdBatch][3]) {
+  using C = WsCfg<R>;
+  const int ntask = reinterpret_cast<const int*>(pk)[0] * C::G4;
+  const unsigned char* mks = pk + L.mask;
+  float* xs_st = reinterpret_cast<float*>(sm + A.sm.xs) + (size_t)st * A.nnmax * C::XR;
+#pragma unroll
+  for (int b = 0; b < kLdBatch; ++b) {
+    const int k = k0 + b * nl;
+    if (k < ntask) {
+      const int ln = k / C::G4, g = k - ln * C::G4;
+      put_row<R>(xs_st, ln, g, mks[ln], v[b]);
+    }
   }
 }
 
-// element data of tile i (coordinates and materials in buffer set b) -> geo stage st;
-// thread `lane` of the geometry warp
-__device__ __forceinline__ void ws_geometry(const WsArgs& A, const Stg& c, int i, int b, int st, int lane) {
-  const unsigned char* pk = c.pk(A, i);
-  const int ne = reinterpret_cast<const int*>(pk)[1];
-  const float4* crd = reinterpret_cast<const float4*>(c.sm + A.sm.crd) + (size_t)b * A.nnmax;
-  const float4* mat = reinterpret_cast<const float4*>(c.sm + A.sm.mat) + (size_t)b * A.te;
-  float* geo = reinterpret_cast<float*>(c.sm + A.sm.geo) + (size_t)st * A.te * kGeoWs;
-  for (int le = lane; le < ne; le += 32) {
-    const uint16_t* eo = reinterpret_cast<const uint16_t*>(pk + c.L.eoff) + le * 16;
-    const unsigned c01 = *reinterpret_cast<const unsigned*>(eo + 10);   // local ids of corners 0, 1
-    const unsigned c23 = *reinterpret_cast<const unsigned*>(eo + 12);   // corners 2, 3
-    const float4 x0 = crd[c01 & 0xffff], x1 = crd[c01 >> 16], x2 = crd[c23 & 0xffff], x3 = crd[c23 >> 16];
-    const float d1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
-    const float d2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
-    const float d3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
-    const float e23[3] = {d2[1] * d3[2] - d2[2] * d3[1], d2[2] * d3[0] - d2[0] * d3[2], d2[0] * d3[1] - d2[1] * d3[0]};
-    const float e31[3] = {d3[1] * d1[2] - d3[2] * d1[1], d3[2] * d1[0] - d3[0] * d1[2], d3[0] * d1[1] - d3[1] * d1[0]};
-    const float e12[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
-    const float det = d1[0] * e23[0] + d1[1] * e23[1] + d1[2] * e23[2];
-    const float inv = 1.f / det;
-    float g[4][3];
+// Element data of element le of a tile (its packet's coordinates and materials):
+// gradients g of the volume coordinates, -g, 4g, lam V/5, 2 mu V/5, mu V/5, 0.
+__device__ __forceinline__ void geo_compute(const unsigned char* pk, const WsLayout& L, int le, float (&v)[kGeoWs]) {
+  const float4* crd = reinterpret_cast<const float4*>(pk + L.crd);
+  const float4* mat = reinterpret_cast<const float4*>(pk + L.mat);
+  const uint16_t* eo = reinterpret_cast<const uint16_t*>(pk + L.eoff) + le * 16;
+  const unsigned c01 = *reinterpret_cast<const unsigned*>(eo + 10);   // local ids of corners 0, 1
+  const unsigned c23 = *reinterpret_cast<const unsigned*>(eo + 12);   // corners 2, 3
+  const float4 x0 = crd[c01 & 0xffff], x1 = crd[c01 >> 16], x2 = crd[c23 & 0xffff], x3 = crd[c23 >> 16];
+  const float d1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
+  const float d2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
+  const float d3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
+  const float e23[3] = {d2[1] * d3[2] - d2[2] * d3[1], d2[2] * d3[0] - d2[0] * d3[2], d2[0] * d3[1] - d2[1] * d3[0]};
+  const float e31[3] = {d3[1] * d1[2] - d3[2] * d1[1], d3[2] * d1[0] - d3[0] * d1[2], d3[0] * d1[1] - d3[1] * d1[0]};
+  const float e12[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
+  const float det = d1[0] * e23[0] + d1[1] * e23[1] + d1[2] * e23[2];
+  const float inv = 1.f / det;
+  float g[4][3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    g[1][q] = e23[q] * inv;
+    g[2][q] = e31[q] * inv;
+    g[3][q] = e12[q] * inv;
+    g[0][q] = -(g[1][q] + g[2][q] + g[3][q]);
+  }
+  const float4 em = mat[le];
+  const float onu = 1.f + em.y;
+  const float mu = em.x / (2.f * onu);
+  const float lam = (em.x * em.y) / (onu * (1.f - 2.f * em.y));
+  const float f = det * (1.f / 30.f);   // 4 V / 20 with V = det / 6
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      g[1][q] = e23[q] * inv;
-      g[2][q] = e31[q] * inv;
-      g[3][q] = e12[q] * inv;
-      g[0][q] = -(g[1][q] + g[2][q] + g[3][q]);
+      v[3 * k + q] = g[k][q];
+      v[12 + 3 * k + q] = -g[k][q];
+      v[24 + 3 * k + q] = 4.f * g[k][q];
     }
-    const float4 em = mat[le];
-    const float onu = 1.f + em.y;
-    const float mu = em.x / (2.f * onu);
-    const float lam = (em.x * em.y) / (onu * (1.f - 2.f * em.y));
-    const float f = det * (1.f / 30.f);   // 4 V / 20 with V = det / 6
-    float v[kGeoWs];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        v[3 * k + q] = g[k][q];
-        v[12 + 3 * k + q] = -g[k][q];
-        v[24 + 3 * k + q] = 4.f * g[k][q];
-      }
-    v[36] = lam * f;
-    v[37] = 2.f * mu * f;
-    v[38] = mu * f;
-    v[39] = 0.f;
-    float4* d = reinterpret_cast<float4*>(geo + le * kGeoWs);
-#pragma unroll
-    for (int q = 0; q < kGeoWs / 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  }
+  v[36] = lam * f;
+  v[37] = 2.f * mu * f;
+  v[38] = mu * f;
+  v[39] = 0.f;
 }
-
+__device__ __forceinline__ void geo_store(const WsArgs& A, unsigned char* sm, int st, int le, const float (&v)[kGeoWs]) {
+  float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(sm + A.sm.geo) + ((size_t)st * A.te + le) * kGeoWs);
+#pragma unroll
+  for (int q = 0; q < kGeoWs / 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
 __device__ __forceinline__ void add4(float4& a, const float4 b) {
   const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
   const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
   a = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// node sums of tile i in stage st by the summing threads r0 = 0 .. NR - 1: task
-// (virtual node v, group g of 4 cases), four incidences per step with their loads
-// in flight
+// One node-sum task (virtual node v, group g of 4 cases): what it needs from the
+// packet, read before the tile's slots are ready.
+struct SumTask {
+  int n;          // incidences (0: no task)
+  int g, mk;
+  bool ow;        // constrained components are written by this task ((I - P) x)
+  int64_t gi;     // offset of the group's 12 values in x and y
+  int o[kVnMax];  // slot offsets of the incidences
+};
+
 template <int R>
-__device__ __forceinline__ void node_sums(const WsArgs& A, const Stg& c, int i, int st, int r0, int NR) {
+__device__ __forceinline__ void sum_fetch(const unsigned char* pk, const WsLayout& L, int k, SumTask& t) {
   using C = WsCfg<R>;
-  const unsigned char* pk = c.pk(A, i);
   const int nv = reinterpret_cast<const int*>(pk)[2];
-  const int* ids = reinterpret_cast<const int*>(pk + c.L.ids);
-  const unsigned char* mks = pk + c.L.mask;
-  const unsigned char* own = pk + c.L.own;
-  const unsigned* vn = reinterpret_cast<const unsigned*>(pk + c.L.vn);
-  const uint16_t* io = reinterpret_cast<const uint16_t*>(pk + c.L.inc_off);
-  const float* obs = reinterpret_cast<const float*>(c.sm + A.sm.ob) + (size_t)st * A.te * C::S;
-  for (int k = r0; k < nv * C::G4; k += NR) {
-    const int v = k / C::G4, g = k - v * C::G4;
-    const unsigned w = vn[v];
-    const int ln = (int)(w & 0xfff);
-    const bool first = (w >> 12) & 1;
-    int j = (int)(w >> 17);
-    const int j1 = j + (int)((w >> 13) & 0xf);
-    const float* b = obs + 4 * g;
-    float4 a[2][3];
+  t.n = 0;
+  if (k >= nv * C::G4) return;
+  const int v = k / C::G4;
+  t.g = k - v * C::G4;
+  const unsigned w = reinterpret_cast<const unsigned*>(pk + L.vn)[v];
+  const int ln = (int)(w & 0xfff);
+  const int j = (int)(w >> 17);
+  t.n = (int)((w >> 13) & 0xf);
+  t.mk = pk[L.mask + ln];
+  t.ow = ((w >> 12) & 1) && pk[L.own + ln] != 0;
+  t.gi = (int64_t)reinterpret_cast<const int*>(pk + L.ids)[ln] * C::XR + 12 * t.g;
+  const uint16_t* io = reinterpret_cast<const uint16_t*>(pk + L.inc_off);
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+  for (int u = 0; u < kVnMax; ++u) t.o[u] = u < t.n ? io[j + u] : 0;
+}
+
+// the task's sums over its incidences' slots (stage st) added into y, four incidences
+// with their loads in flight at a time
+template <int R>
+__device__ __forceinline__ void sum_run(const WsArgs& A, const unsigned char* sm, int st, const SumTask& t) {
+  using C = WsCfg<R>;
+  if (t.n == 0) return;
+  const float* b = reinterpret_cast<const float*>(sm + A.sm.ob) + (size_t)st * A.te * C::S + 4 * t.g;
+  float4 a[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) a[h][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (; j + 3 < j1; j += 4) {
-      int o[4];
+  for (int q = 0; q < 3; ++q) a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nn_ = t.n;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) o[u] = io[j + u];
+  for (int h = 0; h < kVnMax; h += 4) {
+    if (h < nn_) {
       float4 x4[4][3];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
+        if (h + u < nn_)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) x4[u][q] = *reinterpret_cast<const float4*>(b + o[u] + q * R);
+          for (int q = 0; q < 3; ++q) x4[u][q] = *reinterpret_cast<const float4*>(b + t.o[h + u] + q * R);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
+        if (h + u < nn_)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) add4(a[u & 1][q], x4[u][q]);
+          for (int q = 0; q < 3; ++q) add4(a[q], x4[u][q]);
     }
-    for (; j < j1; ++j) {
-      const int o0 = io[j];
+  }
+  // component-major sums -> the node's [case][comp] values of the group
+  const float f[12] = {a[0].x, a[1].x, a[2].x, a[0].y, a[1].y, a[2].y, a[0].z, a[1].z, a[2].z, a[0].w, a[1].w, a[2].w};
+  float* yg = A.y + t.gi;
+  if (t.mk == 7) {
+    atomicAdd(reinterpret_cast<float4*>(yg), make_float4(f[0], f[1], f[2], f[3]));
+    atomicAdd(reinterpret_cast<float4*>(yg) + 1, make_float4(f[4], f[5], f[6], f[7]));
+    atomicAdd(reinterpret_cast<float4*>(yg) + 2, make_float4(f[8], f[9], f[10], f[11]));
+  } else {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) add4(a[0][q], *reinterpret_cast<const float4*>(b + o0 + q * R));
+    for (int q = 0; q < 12; ++q) {
+      if ((t.mk >> (q % 3)) & 1)
+        atomicAdd(yg + q, f[q]);
+      else if (t.ow)
+        yg[q] = __ldg(A.x + t.gi + q);   // constrained DOF: (I - P) x, written once by the node's first tile
     }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) add4(a[0][q], a[1][q]);
-    // component-major sums -> the node's [case][comp] values of the group
-    const float4 a0 = a[0][0], a1 = a[0][1], a2 = a[0][2];
-    const float f[12] = {a0.x, a1.x, a2.x, a0.y, a1.y, a2.y, a0.z, a1.z, a2.z, a0.w, a1.w, a2.w};
-    const int64_t gi = (int64_t)ids[ln] * C::XR + 12 * g;
-    float* yg = A.y + gi;
-    const int mk = mks[ln];
-    if (mk == 7) {
-      atomicAdd(reinterpret_cast<float4*>(yg), make_float4(f[0], f[1], f[2], f[3]));
-      atomicAdd(reinterpret_cast<float4*>(yg) + 1, make_float4(f[4], f[5], f[6], f[7]));
-      atomicAdd(reinterpret_cast<float4*>(yg) + 2, make_float4(f[8], f[9], f[10], f[11]));
-    } else {
-      const bool ow = first && own[ln] != 0;
-#pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        if ((mk >> (q % 3)) & 1)
-          atomicAdd(yg + q, f[q]);
-        else if (ow)
-          yg[q] = __ldg(A.x + gi + q);   // constrained DOF: (I - P) x, written once by the node's first tile
+  }
+}
+
+// Staging roles. Each runs its own loop over the CTA's tiles i = 0 .. n - 1; before
+// waiting for tile i's products (DONE), it does the work that needs only packets.
+struct Stg {
+  uint32_t mb;
+  int64_t t0, G;
+  int n;
+  __device__ uint32_t pkf(const WsArgs& A, int i) const { return mb + kPkf + 8 * (i % A.npk); }
+  __device__ uint32_t pkpar(const WsArgs& A, int i) const { return (uint32_t)((i / A.npk) & 1); }
+  __device__ uint32_t done(int i) const { return mb + kDone + 8 * (i & 1); }
+  __device__ uint32_t ready(int i) const { return mb + kReady + 8 * (i & 1); }
+};
+
+// one thread: the packet of tile i into its slot, completion counted on PKF
+__device__ __forceinline__ void issue_packet(const WsArgs& A, unsigned char* sm, const Stg& c, int i) {
+  unsigned char* dst = sm + A.sm.pk + (i % A.npk) * A.pk;
+  fence_proxy_async();
+  mbar_arrive_tx(c.pkf(A, i), (uint32_t)A.pk);
+  bulk_g2s(dst, A.packets + (c.t0 + (int64_t)i * c.G) * A.pk, (uint32_t)A.pk, c.pkf(A, i));
+}
+
+// loaders: node rows of tile i + 2 into stage i & 1 (tiles 0 and 1 before the loop)
+template <int R>
+__device__ __forceinline__ void role_load(const WsArgs& A, unsigned char* sm, const WsLayout& L, const Stg& c, int lt,
+                                          int NL, bool& ok) {
+  using C = WsCfg<R>;
+  for (int j = -2; j < c.n - 2; ++j) {
+    const int t = j + 2;   // tile whose rows this iteration stages
+    float4 rv[kLdBatch][3];
+    mbar_wait(A.status, A.timeout, c.pkf(A, t), c.pkpar(A, t), ok);
+    const unsigned char* pk = pk_at(A, sm, t);
+    rows_fetch<R>(A, pk, L, lt, NL, rv);
+    if (j >= 0) mbar_wait(A.status, A.timeout, c.done(j), (uint32_t)((j >> 1) & 1), ok);   // stage free
+    rows_put<R>(A, sm, pk, L, t & 1, lt, NL, rv);
+    const int ntask = reinterpret_cast<const int*>(pk)[0] * C::G4;
+    for (int k0 = lt + kLdBatch * NL; k0 < ntask; k0 += kLdBatch * NL) {
+      rows_fetch<R>(A, pk, L, k0, NL, rv);
+      rows_put<R>(A, sm, pk, L, t & 1, k0, NL, rv);
+    }
+    mbar_arrive(c.ready(t));
+  }
+  for (int i = c.n - 2; i < c.n; ++i)   // the last two tiles: nothing to stage, DONE still waited
+    if (i >= 0) mbar_wait(A.status, A.timeout, c.done(i), (uint32_t)((i >> 1) & 1), ok);
+}
+
+// geometry warp: element data of tile i + 2 into stage i & 1
+__device__ __forceinline__ void role_geo(const WsArgs& A, unsigned char* sm, const WsLayout& L, const Stg& c, int lane,
+                                         bool& ok) {
+  for (int j = -2; j < c.n - 2; ++j) {
+    const int t = j + 2;
+    float gv[kGeoWs];
+    mbar_wait(A.status, A.timeout, c.pkf(A, t), c.pkpar(A, t), ok);
+    const unsigned char* pk = pk_at(A, sm, t);
+    const int ne = reinterpret_cast<const int*>(pk)[1];
+    if (lane < ne) geo_compute(pk, L, lane, gv);
+    if (j >= 0) mbar_wait(A.status, A.timeout, c.done(j), (uint32_t)((j >> 1) & 1), ok);
+    if (lane < ne) geo_store(A, sm, t & 1, lane, gv);
+    for (int le = lane + 32; le < ne; le += 32) {
+      geo_compute(pk, L, le, gv);
+      geo_store(A, sm, t & 1, le, gv);
+    }
+    mbar_arrive(c.ready(t));
+  }
+  for (int i = c.n - 2; i < c.n; ++i)
+    if (i >= 0) mbar_wait(A.status, A.timeout, c.done(i), (uint32_t)((i >> 1) & 1), ok);
+}
+
+// summing threads: node sums of tile i (stage i & 1) into y, then the packet of tile
+// i + npk into tile i's packet slot
+template <int R>
+__device__ __forceinline__ void role_sum(const WsArgs& A, unsigned char* sm, const WsLayout& L, const Stg& c, int sumt,
+                                         int NS, int& last_pk, bool& ok) {
+  using C = WsCfg<R>;
+  for (int j = 0; j < 2 && j < c.n; ++j) mbar_arrive(c.ready(j));   // stages 0 and 1 hold no earlier sums
+  for (int i = 0; i < c.n; ++i) {
+    SumTask tk;
+    mbar_wait(A.status, A.timeout, c.pkf(A, i), c.pkpar(A, i), ok);   // tile i's packet landed
+    const unsigned char* pk = pk_at(A, sm, i);
+    sum_fetch<R>(pk, L, sumt, tk);
+    mbar_wait(A.status, A.timeout, c.done(i), (uint32_t)((i >> 1) & 1), ok);   // tile i computed
+    sum_run<R>(A, sm, i & 1, tk);
+    const int ntask = reinterpret_cast<const int*>(pk)[2] * C::G4;
+    for (int k = sumt + NS; k < ntask; k += NS) {
+      sum_fetch<R>(pk, L, k, tk);
+      sum_run<R>(A, sm, i & 1, tk);
+    }
+    if (i + 2 < c.n) mbar_arrive(c.ready(i + 2));
+    if (i + A.npk < c.n) {
+      bar_sync(kBarSum, NS);              // every summing thread is done with tile i's packet
+      if (sumt == 0) {
+        issue_packet(A, sm, c, i + A.npk);
+        last_pk = i + A.npk;
       }
     }
   }
 }
 
 template <int R, int NT>
-__device__ __forceinline__ void ws_staging(const WsArgs& A, unsigned char* sm, const WsLayout& L, int n_it,
-                                           int64_t t0, int64_t G, bool& ok) {
-  const uint32_t mb = smem_u32(sm);   // READY[s] at mb + 8 s, DONE[s] at mb + 16 + 8 s
-  const int mt = threadIdx.x - A.cw * 32;
+__device__ __forceinline__ void ws_staging(const WsArgs& A, unsigned char* sm, const WsLayout& L, int n, int64_t t0,
+                                           int64_t G, bool& ok) {
+  const int mt = threadIdx.x - A.cw * 32;   // staging thread 0 .. NM - 1
   const int NM = NT - A.cw * 32;
-  const Stg c{sm, L, n_it, mt, NM, t0, G};
-  const Stg cl{sm, L, n_it, mt - 32, 32 * kLoaderWarps, t0, G};   // the loader warps' view
-  const int n = n_it;
   const int wid = mt >> 5;
-  // prologue (all staging threads): packets of the first five tiles; stages of tiles
-  // 0 and 1; rows and geometry inputs of tile 2
-  for (int k = 0; k < kPkSlots && k < n; ++k) issue_packet(A, c, k);
-  cp_commit();
-  cp_wait<0>();
-  bar_sync(kBarStaging, NM);
-  for (int k = 0; k < 2 && k < n; ++k) {
-    issue_rows<R>(A, c, k);
-    issue_geo_inputs(A, c, k, k);
-    cp_commit();
-    cp_wait<0>();
-    bar_sync(kBarStaging, NM);
-    transpose_rows<R>(A, c, k, k);
-    if (wid == 0) ws_geometry(A, c, k, k, k, mt);
-    bar_sync(kBarStaging, NM);   // raw rows consumed
-    mbar_arrive(mb + 8 * k);
-  }
-  if (n > 2) {
-    issue_rows<R>(A, c, 2);
-    issue_geo_inputs(A, c, 2, 0);
-  }
-  cp_commit();
-  cp_commit();   // (empty) in place of a packet group: each iteration commits rows, then packets
-  for (int i = 0; i < n; ++i) {
-    const int st = i & 1;
-    const bool next = i + 2 < n;
-    mbar_wait(A.status, A.timeout, mb + 16 + 8 * st, (uint32_t)((i >> 1) & 1), ok);   // tile i computed
-    cp_wait<1>();                  // rows and geometry inputs of tile i + 2 (the latest packet may pend)
-    bar_sync(kBarStaging, NM);
-    if (wid == 0) {
-      if (next) ws_geometry(A, c, i + 2, st, st, mt);
-    } else if (wid <= kLoaderWarps) {
-      if (next) transpose_rows<R>(A, cl, i + 2, st);
-      bar_sync(kBarLoad, 32 * kLoaderWarps);   // raw rows consumed
-      if (i + 3 < n) {
-        issue_rows<R>(A, cl, i + 3);
-        issue_geo_inputs(A, cl, i + 3, (i + 3) & 1);
-      }
-    } else {
-      node_sums<R>(A, c, i, st, mt - 32 * (1 + kLoaderWarps), NM - 32 * (1 + kLoaderWarps));
+  const Stg c{smem_u32(sm), t0, G, n};
+  int last_pk = -1;   // the latest packet this thread issued
+  if (mt == 0)        // packets of the first npk tiles
+    for (int k = 0; k < A.npk && k < n; ++k) {
+      issue_packet(A, sm, c, k);
+      last_pk = k;
     }
-    cp_commit();
-    bar_sync(kBarStaging, NM);     // tile i + 2 staged, tile i summed: its packet slot and slots free
-    if (i + kPkSlots < n) issue_packet(A, c, i + kPkSlots);
-    cp_commit();
-    if (next) mbar_arrive(mb + 8 * st);
-  }
-  cp_wait<0>();
+  if (wid == 0)
+    role_geo(A, sm, L, c, mt, ok);
+  else if (wid <= A.nlw)
+    role_load<R>(A, sm, L, c, mt - 32, 32 * A.nlw, ok);
+  else
+    role_sum<R>(A, sm, L, c, mt - 32 * (1 + A.nlw), NM - 32 * (1 + A.nlw), last_pk, ok);
+  if (!ok)   // a wait gave up: let the packet copies this thread issued land before the CTA exits
+    for (int k = std::max(0, last_pk - A.npk + 1); k <= last_pk; ++k)
+      mbar_drain(A.timeout, c.pkf(A, k), c.pkpar(A, k));
 }
 
 template <int R, int NT>
 __global__ void __launch_bounds__(NT, kWsThreads / NT) ebe_ws_kernel(const WsArgs A) {
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm[];
   if (A.skip && *A.skip) return;
   const int64_t G = gridDim.x, t0 = blockIdx.x;
   if (t0 >= A.n_tiles) return;
@@ -606,10 +669,12 @@ __global__ void __launch_bounds__(NT, kWsThreads / NT) ebe_ws_kernel(const WsArg
   const WsLayout L(A.nnmax, A.nvmax, A.te);
   if (threadIdx.x == 0) {
     const uint32_t mb = smem_u32(sm);
-    mbar_init(mb, NT - 32 * A.cw);                // READY[0], READY[1]: every staging thread
-    mbar_init(mb + 8, NT - 32 * A.cw);
-    mbar_init(mb + 16, 32 * A.cw);                // DONE[0], DONE[1]: every compute thread
-    mbar_init(mb + 24, 32 * A.cw);
+    mbar_init(mb + kReady, NT - 32 * A.cw);        // READY[0], READY[1]: every staging thread
+    mbar_init(mb + kReady + 8, NT - 32 * A.cw);
+    mbar_init(mb + kDone, 32 * A.cw);              // DONE[0], DONE[1]: every compute thread
+    mbar_init(mb + kDone + 8, 32 * A.cw);
+    for (int k = 0; k < A.npk; ++k)                // PKF[k]: one arrival with the expected bytes
+      mbar_init(mb + kPkf + 8 * k, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
@@ -620,11 +685,27 @@ __global__ void __launch_bounds__(NT, kWsThreads / NT) ebe_ws_kernel(const WsArg
     ws_staging<R, NT>(A, sm, L, n_it, t0, G, ok);
 }
 
+// Materials of every element slot of every packet from matv (after a material
+// change, and once when the packets are built).
+__global__ void ws_refresh_mat_kernel(unsigned char* packets, int64_t n_tiles, int pk, int te, int mat_off,
+                                      int elem_off, const float4* matv) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_tiles * te) return;
+  const int64_t t = k / te;
+  const int le = (int)(k - t * te);
+  unsigned char* p = packets + t * (int64_t)pk;
+  const int ne = reinterpret_cast<const int*>(p)[1];
+  float4* mat = reinterpret_cast<float4*>(p + mat_off);
+  const int* el = reinterpret_cast<const int*>(p + elem_off);
+  mat[le] = le < ne ? matv[el[le]] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------
 // host: greedy tiles and packets
 // ---------------------------------------------------------------------------
-// Partition of the elements into tiles of at most te elements (see the file header).
-void greedy_tiles(const fe_mesh* m, int te, std::vector<int32_t>& elems, std::vector<int64_t>& tptr) {
+// Partition of the elements into tiles of at most te elements and nncap nodes (see the
+// file header).
+void greedy_tiles(const fe_mesh* m, int te, int nncap, std::vector<int32_t>& elems, std::vector<int64_t>& tptr) {
   const int64_t E = m->n_elem, N = m->n_nodes;
   const int32_t* cn = m->conn_host.data();
   std::vector<int64_t> np((size_t)N + 1, 0);
@@ -700,6 +781,7 @@ void greedy_tiles(const fe_mesh* m, int te, std::vector<int32_t>& elems, std::ve
         if (nxt >= E) break;
         best = (int32_t)nxt;
       }
+      if ((int)marked.size() + 10 - (int)score[(size_t)best] > nncap) break;   // node budget of a tile
       add(best);
     }
     tptr.push_back((int64_t)elems.size());
@@ -715,9 +797,26 @@ void greedy_tiles(const fe_mesh* m, int te, std::vector<int32_t>& elems, std::ve
 
 bool ws_supported(int R) { return R == 4 || R == 8 || R == 16 || R == 32; }
 
+// Loader warps of a block with sw staging warps (one geometry warp, the rest sum nodes).
+static int ws_loader_warps(int sw) { return sw >= 8 ? 3 : 2; }
+
 static int ws_compute_warps(int te, int R) {
   const int t = te * (R / 2);
   return (t % 32 == 0) ? t / 32 : -1;
+}
+
+static void refresh_tiling_materials(const fe_mesh* m, const WsTiling& t, cudaStream_t s) {
+  const WsLayout L(t.nnmax, t.nvmax, t.te);
+  const int64_t n = t.n_tiles * t.te;
+  if (n == 0) return;
+  ws_refresh_mat_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.packets.as<unsigned char>(), t.n_tiles,
+                                                                    t.pk_bytes, t.te, L.mat, L.elem,
+                                                                    m->matv.as<float4>());
+  FE_CHECK_LAUNCH();
+}
+
+void ws_refresh_materials(fe_mesh* m, cudaStream_t s) {
+  for (auto& kv : m->ws_tilings) refresh_tiling_materials(m, *kv.second, s);
 }
 
 const WsTiling* get_ws_tiling(fe_mesh* m, int te, int R, cudaStream_t s) {
@@ -728,17 +827,9 @@ const WsTiling* get_ws_tiling(fe_mesh* m, int te, int R, cudaStream_t s) {
   const int key = te * 256 + R;
   auto found = m->ws_tilings.find(key);
   if (found != m->ws_tilings.end()) return found->second.get();
-  if (!m->xyz4.ptr) {
-    std::vector<float> c4((size_t)m->n_nodes * 4, 0.f);
-    for (int64_t n = 0; n < m->n_nodes; ++n)
-      for (int i = 0; i < 3; ++i) c4[(size_t)(4 * n + i)] = (float)m->xyz_host[(size_t)(3 * n + i)];
-    m->xyz4.alloc(c4.size() * sizeof(float));
-    FE_CUDA(cudaMemcpyAsync(m->xyz4.ptr, c4.data(), m->xyz4.bytes, cudaMemcpyHostToDevice, s));
-    FE_CUDA(cudaStreamSynchronize(s));
-  }
   std::vector<int32_t> elems;
   std::vector<int64_t> tptr;
-  greedy_tiles(m, te, elems, tptr);
+  greedy_tiles(m, te, ws_node_cap(te), elems, tptr);
   const int64_t nt = (int64_t)tptr.size() - 1;
   const int XR = 3 * R, S = ws_slot_stride(R);
   FE_REQUIRE((int64_t)te * S + 10 * XR < 65536, "tile of %d elements too large for 16-bit slot offsets", te);
@@ -792,9 +883,11 @@ const WsTiling* get_ws_tiling(fe_mesh* m, int te, int R, cudaStream_t s) {
     const int ne = (int)(tptr[(size_t)t + 1] - tptr[(size_t)t]);
     std::memcpy(b + L.ids, tn.data(), (size_t)nn * 4);
     std::memcpy(b + L.elem, &elems[(size_t)tptr[(size_t)t]], (size_t)ne * 4);
+    float* crd = reinterpret_cast<float*>(b + L.crd);
     for (int i = 0; i < nn; ++i) {
       const int32_t g = tn[(size_t)i];
       lid[(size_t)g] = i;
+      for (int c = 0; c < 3; ++c) crd[4 * i + c] = (float)m->xyz_host[(size_t)(3 * (int64_t)g + c)];
       b[L.mask + i] = m->nmask_host[(size_t)g];
       b[L.own + i] = seen[(size_t)g] ? 0 : 1;
       seen[(size_t)g] = 1;
@@ -844,33 +937,40 @@ const WsTiling* get_ws_tiling(fe_mesh* m, int te, int R, cudaStream_t s) {
   tp->nodes_per_elem = (double)node_sum / (double)m->n_elem;
   tp->packets.alloc(pk.size());
   FE_CUDA(cudaMemcpyAsync(tp->packets.ptr, pk.data(), pk.size(), cudaMemcpyHostToDevice, s));
+  refresh_tiling_materials(m, *tp, s);
   FE_CUDA(cudaStreamSynchronize(s));
   const WsTiling* out = tp.get();
   m->ws_tilings[key] = std::move(tp);
   return out;
 }
 
-static int max_smem_optin_ws(int device) {
-  int v = 0;
-  FE_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-  return v;
+// Shared memory a block of nth threads may use: the opt-in maximum for one block
+// per SM, half of the SM's shared memory (less the per-block reservation) for two.
+static int ws_smem_budget(int device, int nth) {
+  int optin = 0, per_sm = 0, reserved = 0;
+  FE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  if (nth == kWsThreads) return optin;
+  FE_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  FE_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+  return std::min(optin, per_sm / 2 - reserved);
 }
 
-// The tiling fits when its buffers fit in shared memory and the block keeps at
-// least 4 staging warps (geometry, two loaders, node sums); 256-thread blocks
-// (two per SM) also need two blocks' buffers to fit in one SM.
+// Packet slots that fit beside the tile's other buffers (at most kPkMax; fewer than
+// kPkMin means the tiling does not fit).
+static int ws_packet_slots(const WsTiling& t, int R, int budget) {
+  const WsSmem base(t.te, R, t.nnmax, t.pk_bytes, 0);
+  if (base.bytes >= budget) return 0;
+  return std::min(kPkMax, (budget - base.bytes) / t.pk_bytes);
+}
+
+// The tiling fits when its buffers fit in shared memory with at least kPkMin packet
+// slots and the block keeps at least 4 staging warps (geometry, two loaders, node sums).
 bool ws_fits(fe_mesh* m, int te, int R, int nth) {
   if (!ws_supported(R) || (nth != kWsThreads && nth != kWsThreads / 2)) return false;
   const int cw = ws_compute_warps(te, R);
   if (cw < 1 || cw > nth / 32 - 4) return false;
   const WsTiling* t = get_ws_tiling(m, te, R, nullptr);
-  const WsSmem sm(te, R, t->nnmax, t->pk_bytes);
-  if (sm.bytes > max_smem_optin_ws(m->device)) return false;
-  if (nth == kWsThreads) return true;
-  int per_sm = 0, reserved = 0;
-  FE_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device));
-  FE_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device));
-  return 2 * (sm.bytes + reserved) <= per_sm;
+  return ws_packet_slots(*t, R, ws_smem_budget(m->device, nth)) >= kPkMin;
 }
 
 template <int R, int NT>
@@ -882,19 +982,19 @@ static void launch_ws_r(const fe_mesh* m, const WsTiling& t, const float* x, flo
   A.nnmax = t.nnmax;
   A.nvmax = t.nvmax;
   A.pk = t.pk_bytes;
+  A.npk = ws_packet_slots(t, R, ws_smem_budget(m->device, NT));
   A.cw = ws_compute_warps(t.te, R);
+  A.nlw = ws_loader_warps(NT / 32 - A.cw);
   A.packets = t.packets.as<unsigned char>();
-  A.xyz4 = m->xyz4.as<float4>();
-  A.matv = m->matv.as<float4>();
   A.x = x;
   A.y = y;
   A.skip = skip;
   A.status = m->dev_status.as<int>();
   A.timeout = 1LL << 31;   // about one second at 2 GHz
-  A.sm = WsSmem(t.te, R, t.nnmax, t.pk_bytes);
+  A.sm = WsSmem(t.te, R, t.nnmax, t.pk_bytes, A.npk);
   FE_REQUIRE(A.cw >= 1 && A.cw <= NT / 32 - 4, "invalid tile size %d for R = %d with %d threads", t.te, R, NT);
-  FE_REQUIRE(A.sm.bytes <= max_smem_optin_ws(m->device), "warp-specialised tile needs %d B of shared memory",
-             A.sm.bytes);
+  FE_REQUIRE(A.npk >= kPkMin && A.npk <= kPkMax, "warp-specialised tile needs %d B of shared memory",
+             WsSmem(t.te, R, t.nnmax, t.pk_bytes, kPkMin).bytes);
   FE_CUDA(cudaFuncSetAttribute(ebe_ws_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, A.sm.bytes));
   int sms = 0, per_sm = 0;
   FE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
@@ -926,3 +1026,4 @@ void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cu
 }
 
 }  // namespace fe
+

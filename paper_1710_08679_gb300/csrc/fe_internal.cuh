@@ -198,8 +198,9 @@ struct HostPipe {
 
 // Tiles of the warp-specialised EBE kernel (fe_ebe_ws.cu), built per (tile size, R):
 // elements grouped by greedy growth (each tile adds the element sharing most nodes
-// with it), one packet per tile with the tile's node ids, element ids, slot offsets
-// and row offsets for R cases (see WsLayout in fe_ebe_ws.cu).
+// with it), one packet per tile with the tile's node ids and coordinates, element
+// ids and materials, slot offsets and row offsets for R cases (see WsLayout in
+// fe_ebe_ws.cu); the materials are rewritten when the mesh's materials change.
 struct WsTiling {
   int te = 0;             // elements per tile (the last tiles may hold fewer)
   int R = 0;              // cases the offsets are laid out for
@@ -235,8 +236,7 @@ struct fe_mesh {
   std::map<int, std::unique_ptr<fe::Tiling>> tilings;
   // tilings of the warp-specialised kernel, by tile size * 256 + R (built lazily)
   std::map<int, std::unique_ptr<fe::WsTiling>> ws_tilings;
-  fe::DevBuf xyz4;      // float4 [N]: FP32 coordinates padded to 16 bytes (built with the first WS tiling)
-  fe::DevBuf matv;      // float4 [E]: (E, nu, 0, 0) in FP32, 16-byte rows for bulk copies
+  fe::DevBuf matv;      // float4 [E]: (E, nu, 0, 0) in FP32 (copied into the warp-specialised packets)
   fe::DevBuf dev_status;  // int32: set by a kernel whose bounded wait gave up (fe_mesh_device_status)
   std::vector<double> xyz_host;  // [N][3] coordinates as given
   // EBE kernel per precision (0 = FP64, 1 = FP32) and R: -1 = default, else
@@ -294,6 +294,9 @@ bool ws_supported(int R);
 const WsTiling* get_ws_tiling(fe_mesh* m, int tile_elems, int R, cudaStream_t s);
 // nth: threads per block, 512 (FE_EBE_WS, one block per SM) or 256 (FE_EBE_WS2, two)
 bool ws_fits(fe_mesh* m, int tile_elems, int R, int nth);
+// Rewrites the materials held in the packets of every warp-specialised tiling (after
+// the mesh's materials changed).
+void ws_refresh_materials(fe_mesh* m, cudaStream_t s);
 void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip,
                int nth);
 
