@@ -1866,11 +1866,11 @@ extern "C" fe_status fe_block_jacobi(const fe_mesh* mesh, double* binv_dev, void
 // preconditioner: latency-critical loops that must not take the allocator's lock,
 // and processes whose device memory is already reserved by another allocator's
 // pool (a framework's caching allocator), where a fresh cudaMalloc can fail
-// mid-run. The call synchronises its stream (it reads an error flag back). For them fe_block_jacobi_noalloc keeps its
-// scratch (the FP64 [N][9] accumulator of diagonal blocks, the FP32 copy of the
-// inverse the shared kernel also writes, and an error flag) in the fixed
-// file-scope array below instead of allocating it. Every GPU that loads this
-// library holds the array until the process exits.
+// mid-run. For them fe_block_jacobi_noalloc keeps its scratch (the FP64 [N][9]
+// accumulator of diagonal blocks, the FP32 copy of the inverse the shared kernel
+// also writes, and an error flag) in the fixed file-scope array below instead of
+// allocating it. Every GPU that loads this library holds the array until the
+// process exits. The call synchronises its stream (it reads the error flag back).
 // ---------------------------------------------------------------------------
 namespace fe {
 
