@@ -385,18 +385,27 @@ def run_ours(args):
     bytes_alg = ebe_bytes(N, E, R, 4)
     achieved_gbs = bytes_alg / (ebe_ms * 1e-3) / 1e9
     traffic = None
+    ncu = None
     tp = os.path.join(ROOT, "profiles", "ebe_traffic.json")
     if os.path.exists(tp):
         # the committed capture counts only while the kernel's sources are the ones it measured
         try:
             import hashlib
             tj = json.load(open(tp))
-            same_src = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
-                           for f, h in tj.get("source_sha256", {}).items()) and tj.get("source_sha256")
-            if same_src and tj.get("variant") == kernel_desc and tj.get("shape") == list(shape) and tj.get("R") == R:
+            same_src = bool(tj.get("source_sha256")) and all(
+                hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                for f, h in tj.get("source_sha256", {}).items())
+            applies = (same_src and tj.get("variant") == kernel_desc and tj.get("shape") == list(shape)
+                       and tj.get("R") == R)
+            if applies:
                 traffic = tj.get("traffic_bytes_per_launch")
+            ncu = {"kernel": tj.get("kernel"), "counters": tj.get("kernels"), "command": tj.get("command"),
+                   "applies_to_this_run": applies,
+                   "note": "one ncu capture of the committed kernel (DRAM bytes and duration of one launch, "
+                           "cold caches); used for roofline.traffic only while its source hash and "
+                           "configuration match this run"}
         except Exception:
-            traffic = None
+            traffic, ncu = None, None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "fe_ebe_apply (%s + %s EBE kernel)" % (first_pass, kernel_desc),
@@ -412,7 +421,7 @@ def run_ours(args):
                       "l2": "inputs larger than L2 (x and y %d MB each), no flush" % (x.numel() * 4 // 2 ** 20),
                       "parallelism": "case-sharded replicas x%d" % world},
            "e2e": e2e, "gpu_launches": launches_per_product * args.steps, "roofline": roofline, "clocks": clocks,
-           "profiles": "profiles/ebe_crust70x70x35_R16_fp32_launches.md"}
+           "ncu": ncu}
 
     if not args.no_sweep:
         sweep = {}
