@@ -153,6 +153,18 @@ void fe_mesh_destroy(fe_mesh* mesh);
  */
 fe_status fe_mesh_device_status(const fe_mesh* mesh, void* stream);
 
+/*
+ * fe_wait_selftest -- exercises one kind of bounded device-side wait with a wait that
+ * nothing ends (no counterpart in the paper; a test of the failure path without a
+ * GPU fault). which = 0: the mbarrier wait of the warp-specialised EBE kernel, one
+ * warp; which = 1: the grid-wide barrier of the persistent inner-loop kernel, two
+ * blocks of which only one arrives. The wait gives up after `cycles` SM clock cycles
+ * (1 .. 2^32; 2^21 is about a millisecond) and sets the mesh's status word, so the
+ * next fe_mesh_device_status returns FE_ETIMEOUT. which = 1 synchronises `stream`.
+ * FE_EINVAL for a NULL mesh or arguments out of range (nothing is launched).
+ */
+fe_status fe_wait_selftest(const fe_mesh* mesh, int32_t which, int64_t cycles, void* stream);
+
 /* Node and element counts of a mesh. */
 fe_status fe_mesh_info(const fe_mesh* mesh, int64_t* n_nodes, int64_t* n_elem);
 

@@ -473,10 +473,24 @@ fe_status fe_mesh_device_status(const fe_mesh* m, void* stream) {
   });
   if (st != FE_OK) return st;
   if (v != 0) {
-    set_error("a device-side wait of the EBE kernel gave up; the products since the last check are invalid");
+    set_error("a bounded device-side wait gave up; the results of the kernels since the last check are invalid");
     return FE_ETIMEOUT;
   }
   return FE_OK;
+}
+
+fe_status fe_wait_selftest(const fe_mesh* m, int32_t which, int64_t cycles, void* stream) {
+  return guarded([&] {
+    FE_REQUIRE(m != nullptr, "mesh is NULL");
+    FE_REQUIRE(which == 0 || which == 1, "which must be 0 (mbarrier wait) or 1 (grid barrier), got %d", which);
+    FE_REQUIRE(cycles >= 1 && cycles <= (int64_t)1 << 32, "cycles must be in [1, 2^32], got %lld",
+               (long long)cycles);
+    DeviceGuard dg(m->device);
+    if (which == 0)
+      ws_wait_selftest(m, (long long)cycles, (cudaStream_t)stream);
+    else
+      grid_wait_selftest(m, (long long)cycles, (cudaStream_t)stream);
+  });
 }
 
 fe_status fe_mesh_info(const fe_mesh* m, int64_t* n_nodes, int64_t* n_elem) {

@@ -795,6 +795,25 @@ void greedy_tiles(const fe_mesh* m, int te, int nncap, std::vector<int32_t>& ele
 
 }  // namespace
 
+namespace {
+// One warp initialises an mbarrier that expects one arrival, which never comes, and
+// waits on it with the kernel's bounded wait (mbar_wait), limited to `cycles`: the
+// wait gives up, records it in *status and the kernel returns.
+__global__ void mbar_wait_selftest_kernel(int* status, long long cycles) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  __syncthreads();
+  bool ok = true;
+  mbar_wait(status, cycles, b, 0, ok);
+}
+}  // namespace
+
+void ws_wait_selftest(const fe_mesh* m, long long cycles, cudaStream_t s) {
+  mbar_wait_selftest_kernel<<<1, 32, 0, s>>>(m->dev_status.as<int>(), cycles);
+  FE_CHECK_LAUNCH();
+}
+
 bool ws_supported(int R) { return R == 4 || R == 8 || R == 16 || R == 32; }
 
 // Loader warps of a block with sw staging warps (one geometry warp, the rest sum nodes).

@@ -300,6 +300,11 @@ void ws_refresh_materials(fe_mesh* m, cudaStream_t s);
 void launch_ws(const fe_mesh* m, const WsTiling& t, const float* x, float* y, cudaStream_t s, const int* skip,
                int nth);
 
+// Self-tests of the bounded device-side waits (fe_wait_selftest): a wait that nothing
+// ends, limited to `cycles`; each records its timeout in the mesh's status word.
+void ws_wait_selftest(const fe_mesh* m, long long cycles, cudaStream_t s);    // fe_ebe_ws.cu, mbarrier
+void grid_wait_selftest(const fe_mesh* m, long long cycles, cudaStream_t s);  // fe_solver.cu, grid barrier
+
 // Block Jacobi (fe_solver.cu)
 void build_block_jacobi(fe_mesh* m, cudaStream_t s);
 

@@ -921,6 +921,13 @@ __device__ __forceinline__ bool grid_barrier(const InnerArgs& A) {
   return ok_s != 0;
 }
 
+// Two blocks, of which only block 0 reaches the grid-wide barrier: its wait, limited
+// to A.timeout cycles, gives up, raises the abort flag and records it in *A.status.
+__global__ void grid_wait_selftest_kernel(InnerArgs A) {
+  if (blockIdx.x != 0) return;
+  grid_barrier(A);
+}
+
 // q (12 values: 4 cases x 3) of block row a times x, cases r0 .. r0 + 3
 template <bool SLICED>
 __device__ __forceinline__ void row_times(const InnerArgs& A, int64_t a, int r0, const float* __restrict__ x,
@@ -1230,6 +1237,20 @@ struct Solve {
 
 constexpr size_t kPersSums = 2 * 3 * 64 * sizeof(double);   // [2][3][R <= 64]
 constexpr size_t kPersBytes = kPersSums + 64;               // + barrier count, generation, abort flag
+
+void grid_wait_selftest(const fe_mesh* m, long long cycles, cudaStream_t s) {
+  DevBuf words;
+  words.alloc(64);   // barrier count, generation, abort flag
+  FE_CUDA(cudaMemsetAsync(words.ptr, 0, 64, s));
+  InnerArgs A{};
+  A.bar = words.as<unsigned>();
+  A.abort_flag = reinterpret_cast<int*>(words.as<unsigned char>() + 16);
+  A.status = m->dev_status.as<int>();
+  A.timeout = cycles;
+  grid_wait_selftest_kernel<<<2, 32, 0, s>>>(A);
+  FE_CHECK_LAUNCH();
+  FE_CUDA(cudaStreamSynchronize(s));   // the words are freed on return
+}
 
 static SolverWork* get_work(fe_mesh* m, int R) {
   SolverWork* w = m->work;

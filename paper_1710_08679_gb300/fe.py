@@ -36,7 +36,7 @@ EXPORTED = ["fe_last_error", "fe_version", "fe_solve_opts_default", "fe_mesh_cre
             "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply", "fe_level2_info", "fe_level2_apply",
             "fe_level2_restrict", "fe_level2_prolong", "fe_level2_block_jacobi", "fe_coarse_matrix_info",
             "fe_ebe_apply_host", "fe_mesh_device_status", "fe_obs_create", "fe_obs_destroy", "fe_obs_apply",
-            "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots"]
+            "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots", "fe_wait_selftest"]
 
 
 class FeError(RuntimeError):
@@ -107,6 +107,7 @@ def load(path: Optional[str] = None):
     lib.fe_coarse_matrix_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]
     lib.fe_ebe_apply_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp]
     lib.fe_mesh_device_status.argtypes = [_vp, _vp]
+    lib.fe_wait_selftest.argtypes = [_vp, _i32, _i64, _vp]
     lib.fe_obs_create.argtypes = [_vp, _i64, _i32, _vp, _vp, ctypes.POINTER(_vp)]
     lib.fe_obs_destroy.argtypes = [_vp]
     lib.fe_obs_destroy.restype = None
@@ -120,7 +121,8 @@ def load(path: Optional[str] = None):
                  "fe_coarse_restrict", "fe_coarse_prolong", "fe_coarse_block_jacobi", "fe_coarse_apply",
                  "fe_level2_info", "fe_level2_apply", "fe_level2_restrict", "fe_level2_prolong",
                  "fe_level2_block_jacobi", "fe_coarse_matrix_info", "fe_ebe_apply_host", "fe_mesh_device_status",
-                 "fe_obs_create", "fe_obs_apply", "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots"):
+                 "fe_obs_create", "fe_obs_apply", "fe_obs_adjoint", "fe_combine_cases", "fe_case_dots",
+                 "fe_wait_selftest"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -270,6 +272,13 @@ class Mesh:
         """Synchronise the current stream and raise FeError(FE_ETIMEOUT) if a kernel on
         this mesh gave up a bounded device-side wait since the last check."""
         _check(load().fe_mesh_device_status(self._h, self._stream()), "fe_mesh_device_status")
+
+    def wait_selftest(self, which: str = "mbarrier", cycles: int = 1 << 21):
+        """Runs a bounded device-side wait that nothing ends ("mbarrier": the wait of the
+        warp-specialised EBE kernel; "grid": the inner-loop kernel's grid barrier); it
+        gives up after `cycles` SM cycles and the next device_status() raises FE_ETIMEOUT."""
+        _check(load().fe_wait_selftest(self._h, {"mbarrier": 0, "grid": 1}[which], int(cycles), self._stream()),
+               "fe_wait_selftest")
 
     def set_log_young(self, logE):
         torch = _torch()

@@ -84,4 +84,5 @@ def test_null_arguments_rejected():
     assert b"NULL" in lib.fe_last_error()
     assert lib.fe_pcg_solve(None, 1, None, None, None, None, None) == fe.FE_EINVAL
     assert lib.fe_adjoint_grad(None, 1, None, None, None, None) == fe.FE_EINVAL
+    assert lib.fe_wait_selftest(None, 0, 1000, None) == fe.FE_EINVAL
     lib.fe_mesh_destroy(None)
