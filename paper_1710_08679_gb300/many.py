@@ -104,10 +104,11 @@ class CaseStore:
         _save_json(b + ".json", dict(stats, f_sha256=f_digest, case=c))   # a record means a whole file
 
     def get(self, c: int):
+        """(u, statistics) of case c; u is memory-mapped from its file."""
         b = self._base(c)
         with open(b + ".json") as fh:
             meta = json.load(fh)
-        return np.load(b + ".npy"), meta
+        return np.load(b + ".npy", mmap_mode="r"), meta
 
 
 def solve_many_resumable(mesh, f_cases, store_dir: str, chunk: int = 0, R_slots: int = 0,
@@ -118,12 +119,15 @@ def solve_many_resumable(mesh, f_cases, store_dir: str, chunk: int = 0, R_slots:
     `store_dir`. Cases already stored there for the same right-hand side are not
     solved again. `on_chunk(cases)` runs after each chunk is stored (for progress,
     or to stop the run); `key` joins the mesh fingerprint (mesh_fingerprint). Returns
-    (u [n, N, 3] numpy float64, stats list, cases solved by this call)."""
+    (u, stats, solved): u a list of n float64 [N, 3] arrays memory-mapped from the
+    store (so that hundreds of cases of a large mesh need no host memory of their
+    own), the statistics of every case, and the cases solved by this call. Right-hand
+    sides are hashed one case at a time."""
     import torch
 
     n = int(f_cases.shape[0])
     if n == 0:
-        return np.zeros((0, mesh.n_nodes, 3)), [], []
+        return [], [], []
     opts.setdefault("raise_on_fail", False)
     defaults = {k: v.default for k, v in inspect.signature(mesh.solve_many).parameters.items()
                 if v.default is not inspect.Parameter.empty}
@@ -131,8 +135,7 @@ def solve_many_resumable(mesh, f_cases, store_dir: str, chunk: int = 0, R_slots:
     manifest = {"mesh": mesh_fingerprint(mesh, key), "n_nodes": int(mesh.n_nodes),
                 "options": {k: eff[k] for k in _OPTION_KEYS if k in eff}}
     store = CaseStore(store_dir, manifest)
-    f_host = f_cases.detach().cpu().numpy()
-    digests = [_digest(f_host[c]) for c in range(n)]
+    digests = [_digest(f_cases[c].detach().cpu().numpy()) for c in range(n)]
     pending = [c for c in range(n) if not store.done(c, digests[c])]
     solved = []   # cases solved by this call
     while pending:
@@ -154,4 +157,4 @@ def solve_many_resumable(mesh, f_cases, store_dir: str, chunk: int = 0, R_slots:
         u_c, meta = store.get(c)
         us.append(u_c)
         metas.append(meta)
-    return np.stack(us), metas, solved
+    return us, metas, solved

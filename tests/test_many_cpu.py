@@ -36,9 +36,9 @@ def test_full_run_then_nothing_left(tmp_path):
     m, f = FakeMesh(), cases(7)
     u, st, solved = many.solve_many_resumable(m, f, str(tmp_path), chunk=3)
     assert solved == list(range(7)) and m.calls == [3, 3, 1]
-    assert np.array_equal(u, 2.0 * f.numpy()) and all(s["status"] == 0 for s in st)
+    assert np.array_equal(np.stack(u), 2.0 * f.numpy()) and all(s["status"] == 0 for s in st)
     u2, _, solved2 = many.solve_many_resumable(m, f, str(tmp_path), chunk=3)
-    assert solved2 == [] and m.calls == [3, 3, 1] and np.array_equal(u2, u)
+    assert solved2 == [] and m.calls == [3, 3, 1] and np.array_equal(np.stack(u2), np.stack(u))
 
 
 def test_interrupted_run_resumes_with_pending_cases_only(tmp_path):
@@ -53,7 +53,7 @@ def test_interrupted_run_resumes_with_pending_cases_only(tmp_path):
         ["case_00000.json", "case_00001.json", "case_00002.json", "manifest.json"]
     u, _, solved = many.solve_many_resumable(m, f, str(tmp_path), chunk=3)
     assert solved == [3, 4, 5, 6, 7] and m.calls == [3, 3, 2]
-    assert np.array_equal(u, 2.0 * f.numpy())
+    assert np.array_equal(np.stack(u), 2.0 * f.numpy())
 
 
 def test_changed_right_hand_side_is_solved_again(tmp_path):
@@ -62,7 +62,7 @@ def test_changed_right_hand_side_is_solved_again(tmp_path):
     g = f.clone()
     g[2] += 1.0
     u, _, solved = many.solve_many_resumable(m, g, str(tmp_path))
-    assert solved == [2] and np.array_equal(u, 2.0 * g.numpy())
+    assert solved == [2] and np.array_equal(np.stack(u), 2.0 * g.numpy())
 
 
 def test_other_options_or_mesh_are_refused(tmp_path):
